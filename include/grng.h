@@ -1,0 +1,201 @@
+/*
+ * grng.h - C ABI of a GB300 (sm_103a) bulk random number library.
+ *
+ * The interface follows the engine / distribution / generate shape of the
+ * oneMKL RNG domain that the paper extends (Sec. 3.1: engine classes with
+ * `generate` templates parameterised by a distribution object that carries
+ * its own parameters and a custom range), and the native generator flow of
+ * Sec. 3.2 (create a generator, set seed and offset, generate into device
+ * memory, destroy).  The paper's generate(distr, n, r) call (Sec. 3.3,
+ * Listing 1) followed by a separate range-transform kernel (Sec. 3.3,
+ * Listing 2) becomes one call and one kernel here: the transform is fused
+ * into the generator.
+ *
+ * Conventions for every function:
+ *   - Return value: a grng_status; GRNG_OK (0) on success.  No function
+ *     aborts, prints or throws.  On any error the engine is left unchanged.
+ *   - Device pointers must belong to the CUDA device that is current on the
+ *     calling thread; streams (grng_stream_t, ABI-compatible with
+ *     cudaStream_t; NULL = the legacy default stream) likewise.
+ *   - Generation calls are asynchronous with respect to the host: they only
+ *     enqueue work on `stream`; the output is valid once the stream reaches
+ *     that point.  Ordering with other work is stream order.
+ *   - The library owns engines (small host structs, no device memory);
+ *     callers own every buffer and stream they pass in.
+ *   - An engine must not be used by two threads at the same time.  Distinct
+ *     engines may be used concurrently.
+ *
+ * Word streams.  An engine is a stream of 32-bit words w_0, w_1, ... with a
+ * 128-bit word offset.  Philox4x32-10 (Salmon et al., SC'11): key =
+ * (seed mod 2^32, seed >> 32); word g is lane (g mod 4) of the block whose
+ * 128-bit counter is floor(g / 4).  MRG32k3a (L'Ecuyer 1999): seeded state
+ * x1 = (1, 1, seed mod m1), x2 = (1, 1, 1); word n is (x1_n - x2_n) mod m1.
+ * The paper names both engines (Sec. 3.1) but defines neither.
+ *
+ * Words per output (the consumption rule; the paper does not fix one):
+ *   bits U32: 1 | uniform F32: 1 | uniform F64: 2 (the earlier word is the
+ *   high half) | gaussian / lognormal F32: 1, F64: 2, consumed in
+ *   Box-Muller pairs: an odd n still consumes its last pair whole.
+ */
+#ifndef GRNG_H
+#define GRNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GRNG_API __attribute__((visibility("default")))
+#else
+#define GRNG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum grng_status {
+  GRNG_OK = 0,
+  GRNG_ERR_INVALID_ARG = 1, /* null pointer, bad enum, bad parameter, misaligned pointer */
+  GRNG_ERR_UNSUPPORTED = 2, /* valid request the library cannot serve (size limits) */
+  GRNG_ERR_OOM = 3,         /* host allocation failed */
+  GRNG_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+  GRNG_ERR_TIMEOUT = 5,     /* reserved for bounded device waits */
+  GRNG_ERR_BUDGET = 6       /* reserved for admission budgets */
+} grng_status;
+
+typedef enum grng_engine_kind {
+  GRNG_PHILOX4X32X10 = 0,
+  GRNG_MRG32K3A = 1
+} grng_engine_kind;
+
+typedef enum grng_dist_kind {
+  GRNG_BITS = 0,      /* raw 32-bit words; dtype must be GRNG_U32 */
+  GRNG_UNIFORM = 1,   /* [p0, p1) = [a, b) */
+  GRNG_GAUSSIAN = 2,  /* Box-Muller; p0 = mean, p1 = stddev > 0 */
+  GRNG_LOGNORMAL = 3  /* exp(m + s z), z Box-Muller; p0 = m, p1 = s > 0 */
+} grng_dist_kind;
+
+typedef enum grng_dtype { GRNG_U32 = 0, GRNG_F32 = 1, GRNG_F64 = 2 } grng_dtype;
+
+/*
+ * A distribution with its parameters (Sec. 3.1: distribution objects carry
+ * mean / standard deviation or a custom range).  For F32 outputs the
+ * parameters are first rounded to float.
+ *   uniform:  u = (w >> 8) 2^-24 (F32) or ((w_a << 32 | w_b) >> 11) 2^-53
+ *             (F64); r = a + (b - a) u with round-to-nearest multiply and add
+ *             and no fused multiply-add (the range transform of Sec. 3.3,
+ *             Listing 2); r >= b is replaced by the largest value below b.
+ *             Requires finite a < b with b - a finite in the output type.
+ *   gaussian: pair k -> u1 in (0, 1] from its first unit, u2 in [0, 1) from its
+ *             second; z0 = rho cos(2 pi u2), z1 = rho sin(2 pi u2),
+ *             rho = sqrt(-2 ln u1); output mean + stddev z.
+ *   lognormal: exp(m + s z) with z as for gaussian.
+ * Uniform and bits outputs are bit-exact functions of the words; gaussian and
+ * lognormal outputs are within 2e-6 max(1, |x|) (F32) or 1e-14 max(1, |x|)
+ * (F64) of the exact value.
+ */
+typedef struct grng_distribution {
+  int32_t kind;  /* grng_dist_kind */
+  int32_t dtype; /* grng_dtype */
+  double p0;
+  double p1;
+} grng_distribution;
+
+/* Serialisable engine state (checkpoint / resume). */
+typedef struct grng_engine_state {
+  int32_t kind;        /* grng_engine_kind */
+  uint32_t reserved;   /* zero */
+  uint64_t seed;
+  uint64_t offset_lo;  /* 128-bit word offset = offset_lo + 2^64 offset_hi */
+  uint64_t offset_hi;
+} grng_engine_state;
+
+typedef struct grng_engine* grng_engine_t;
+typedef struct CUstream_st* grng_stream_t; /* same type as cudaStream_t */
+
+/* Human-readable name of a status code (static storage; never NULL). */
+GRNG_API const char* grng_status_string(grng_status status);
+
+/* Detail of the last error raised on the calling thread (static per-thread
+ * storage, overwritten by the next failing call; "" if none). */
+GRNG_API const char* grng_last_error(void);
+
+/*
+ * Creates an engine of `kind` seeded with `seed`, positioned at word offset
+ * `offset` (Sec. 3.2: create the generator, then set seed and offset).
+ * *out receives the handle; release it with grng_engine_destroy.
+ * Errors: INVALID_ARG (out NULL, bad kind), OOM.
+ */
+GRNG_API grng_status grng_engine_create(grng_engine_t* out, int32_t kind, uint64_t seed, uint64_t offset);
+
+/* Creates an engine from a saved state (checkpoint / resume). */
+GRNG_API grng_status grng_engine_restore(grng_engine_t* out, const grng_engine_state* state);
+
+/* Copies an engine (same kind, seed and offset; independent afterwards).
+ * oneMKL engines are copy-constructible (Sec. 3.1), cuRAND's are not. */
+GRNG_API grng_status grng_engine_copy(grng_engine_t* out, grng_engine_t src);
+
+/* Advances the engine by n = n_lo + 2^64 n_hi words (mod 2^128).  The next
+ * generate call starts at the new offset. */
+GRNG_API grng_status grng_engine_skip_ahead(grng_engine_t engine, uint64_t n_lo, uint64_t n_hi);
+
+/* Writes the engine's kind, seed and 128-bit word offset to *out. */
+GRNG_API grng_status grng_engine_get_state(grng_engine_t engine, grng_engine_state* out);
+
+/* Releases an engine.  NULL is accepted and ignored. */
+GRNG_API grng_status grng_engine_destroy(grng_engine_t engine);
+
+/* Number of words that n outputs of `dist` consume (written to *words_out). */
+GRNG_API grng_status grng_words_for(const grng_distribution* dist, int64_t n, uint64_t* words_out);
+
+/*
+ * Fills dev_ptr[0 .. n) with n outputs of `dist` drawn from the engine's
+ * words starting at its current offset, then advances the engine's offset by
+ * grng_words_for(dist, n) words (at enqueue time, like a oneMKL engine that
+ * continues its sequence).  One kernel launch on `stream`; no allocation,
+ * no synchronisation.
+ *   dev_ptr: device memory of n elements of the dtype (uint32 / float /
+ *            double), aligned to the element size; any other alignment and
+ *            any word offset are accepted.  May be NULL only when n == 0.
+ *   n == 0:  no-op, returns GRNG_OK, engine unchanged.
+ * Errors: INVALID_ARG (NULL engine/dist, bad kind/dtype pairing, bad
+ * parameters, n < 0, misaligned or NULL dev_ptr), UNSUPPORTED (n > 2^40),
+ * CUDA (launch failed; engine unchanged).
+ */
+GRNG_API grng_status grng_generate(const grng_distribution* dist, grng_engine_t engine, int64_t n,
+                          void* dev_ptr, grng_stream_t stream);
+
+/*
+ * Substream fill in one launch: for s in [0, num_streams), fills
+ * dev_ptr[s * n_per_stream .. (s + 1) * n_per_stream) with n_per_stream
+ * outputs starting at word offset  offset + s * stride  of the engine, where
+ * offset is the engine's current offset and stride = stride_lo + 2^64
+ * stride_hi words (e.g. 2^76 for MRG32k3a substreams, 2^40 for Philox).
+ * The engine's offset is not changed.  Same argument rules as grng_generate;
+ * UNSUPPORTED if num_streams * n_per_stream > 2^40 or num_streams > 2^31.
+ */
+GRNG_API grng_status grng_generate_substreams(const grng_distribution* dist, grng_engine_t engine,
+                                     int64_t n_per_stream, int64_t num_streams,
+                                     uint64_t stride_lo, uint64_t stride_hi, void* dev_ptr,
+                                     grng_stream_t stream);
+
+/*
+ * The RNG-burner flow of Sec. 4.1 / Sec. 6 (generate, then copy the output
+ * to the host): fills host_ptr[0 .. n) like grng_generate, staging through
+ * the caller's device buffer dev_work of work_bytes bytes (at least 2 MiB,
+ * 256-byte aligned), chunk by chunk, copying each chunk device-to-host on
+ * `stream` while the next chunk is generated.  host_ptr should be pinned
+ * (cudaHostAlloc / cudaHostRegister) for full speed; pageable memory works.
+ * Returns after the copies have completed (synchronises `stream`).  The
+ * engine advances as one grng_generate(dist, n) would, and the values equal
+ * those of that call.
+ */
+GRNG_API grng_status grng_generate_host(const grng_distribution* dist, grng_engine_t engine, int64_t n,
+                               void* host_ptr, void* dev_work, size_t work_bytes,
+                               grng_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRNG_H */

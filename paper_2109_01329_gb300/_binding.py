@@ -1,0 +1,294 @@
+"""ctypes binding of libgrng.so (the C ABI of include/grng.h).
+
+Argument marshalling only: every step of generation runs in the library's
+CUDA kernels.  PyTorch supplies device memory (tensors) and the current
+stream.  There is no CPU fallback: if libgrng.so is missing or cannot be
+loaded, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgrng.so")
+
+# enums of grng.h
+OK = 0
+ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET = 1, 2, 3, 4, 5, 6
+PHILOX4X32X10 = 0
+MRG32K3A = 1
+BITS, UNIFORM, GAUSSIAN, LOGNORMAL = 0, 1, 2, 3
+U32, F32, F64 = 0, 1, 2
+
+EXPORTED = ["grng_status_string", "grng_last_error", "grng_engine_create", "grng_engine_restore",
+            "grng_engine_copy", "grng_engine_skip_ahead", "grng_engine_get_state",
+            "grng_engine_destroy", "grng_words_for", "grng_generate",
+            "grng_generate_substreams", "grng_generate_host"]
+
+
+class GrngError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {_status_name(status)}: {detail}")
+        self.status = status
+
+
+class _Dist(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("p0", ctypes.c_double),
+                ("p1", ctypes.c_double)]
+
+
+class _State(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("offset_lo", ctypes.c_uint64),
+                ("offset_hi", ctypes.c_uint64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Loads libgrng.so (built in-tree); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2109_01329_gb300.build` "
+                "(there is no fallback implementation)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.grng_status_string.argtypes = [ctypes.c_int]
+        L.grng_status_string.restype = ctypes.c_char_p
+        L.grng_last_error.argtypes = []
+        L.grng_last_error.restype = ctypes.c_char_p
+        L.grng_engine_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_uint64,
+                                         ctypes.c_uint64]
+        L.grng_engine_restore.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_State)]
+        L.grng_engine_copy.argtypes = [ctypes.POINTER(vp), vp]
+        L.grng_engine_skip_ahead.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64]
+        L.grng_engine_get_state.argtypes = [vp, ctypes.POINTER(_State)]
+        L.grng_engine_destroy.argtypes = [vp]
+        L.grng_words_for.argtypes = [ctypes.POINTER(_Dist), ctypes.c_int64,
+                                     ctypes.POINTER(ctypes.c_uint64)]
+        L.grng_generate.argtypes = [ctypes.POINTER(_Dist), vp, ctypes.c_int64, vp, vp]
+        L.grng_generate_substreams.argtypes = [ctypes.POINTER(_Dist), vp, ctypes.c_int64,
+                                               ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
+                                               vp, vp]
+        L.grng_generate_host.argtypes = [ctypes.POINTER(_Dist), vp, ctypes.c_int64, vp, vp,
+                                         ctypes.c_size_t, vp]
+        for name in EXPORTED[2:]:
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _status_name(status: int) -> str:
+    try:
+        return load().grng_status_string(status).decode()
+    except Exception:  # noqa: BLE001 - naming an error must not raise
+        return f"status {status}"
+
+
+def _check(status: int, where: str) -> None:
+    if status != OK:
+        detail = load().grng_last_error().decode(errors="replace")
+        raise GrngError(status, where, detail)
+
+
+def _split128(v: int):
+    v %= 1 << 128
+    return v & ((1 << 64) - 1), v >> 64
+
+
+@dataclass(frozen=True)
+class Distribution:
+    """A distribution and its parameters (see grng_distribution in grng.h)."""
+
+    kind: int
+    dtype: int
+    p0: float = 0.0
+    p1: float = 0.0
+
+    def _c(self) -> _Dist:
+        return _Dist(self.kind, self.dtype, float(self.p0), float(self.p1))
+
+    @staticmethod
+    def bits() -> "Distribution":
+        return Distribution(BITS, U32)
+
+    @staticmethod
+    def uniform(a: float = 0.0, b: float = 1.0, dtype: int = F32) -> "Distribution":
+        return Distribution(UNIFORM, dtype, a, b)
+
+    @staticmethod
+    def gaussian(mean: float = 0.0, stddev: float = 1.0, dtype: int = F32) -> "Distribution":
+        return Distribution(GAUSSIAN, dtype, mean, stddev)
+
+    @staticmethod
+    def lognormal(m: float = 0.0, s: float = 1.0, dtype: int = F32) -> "Distribution":
+        return Distribution(LOGNORMAL, dtype, m, s)
+
+
+class Engine:
+    """An engine handle (Philox4x32-10 or MRG32k3a) with a 128-bit word offset."""
+
+    def __init__(self, kind: int, seed: int, offset: int = 0, _handle=None):
+        L = load()
+        self._h = ctypes.c_void_p()
+        if _handle is not None:
+            self._h = _handle
+        else:
+            lo, hi = _split128(offset)
+            _check(L.grng_engine_create(ctypes.byref(self._h), kind, seed % (1 << 64), lo),
+                   "grng_engine_create")
+            if hi:
+                _check(L.grng_engine_skip_ahead(self._h, 0, hi), "grng_engine_skip_ahead")
+
+    @classmethod
+    def restore(cls, state: tuple) -> "Engine":
+        kind, seed, offset = state
+        lo, hi = _split128(offset)
+        st = _State(kind, 0, seed % (1 << 64), lo, hi)
+        h = ctypes.c_void_p()
+        _check(load().grng_engine_restore(ctypes.byref(h), ctypes.byref(st)),
+               "grng_engine_restore")
+        return cls(kind, 0, _handle=h)
+
+    def copy(self) -> "Engine":
+        h = ctypes.c_void_p()
+        _check(load().grng_engine_copy(ctypes.byref(h), self._h), "grng_engine_copy")
+        return Engine(self.state[0], 0, _handle=h)
+
+    def skip_ahead(self, n: int) -> None:
+        lo, hi = _split128(n)
+        _check(load().grng_engine_skip_ahead(self._h, lo, hi), "grng_engine_skip_ahead")
+
+    @property
+    def state(self) -> tuple:
+        st = _State()
+        _check(load().grng_engine_get_state(self._h, ctypes.byref(st)), "grng_engine_get_state")
+        return (st.kind, st.seed, st.offset_lo | (st.offset_hi << 64))
+
+    @property
+    def offset(self) -> int:
+        return self.state[2]
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def close(self) -> None:
+        if self._h:
+            load().grng_engine_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+def words_for(dist: Distribution, n: int) -> int:
+    out = ctypes.c_uint64()
+    d = dist._c()
+    _check(load().grng_words_for(ctypes.byref(d), n, ctypes.byref(out)), "grng_words_for")
+    return int(out.value)
+
+
+_TORCH_DTYPES = {}
+
+
+def _torch_dtype_ok(t, dtype: int) -> bool:
+    import torch
+
+    if dtype == F32:
+        return t.dtype == torch.float32
+    if dtype == F64:
+        return t.dtype == torch.float64
+    return t.dtype in (torch.int32, getattr(torch, "uint32", torch.int32))
+
+
+def _stream_ptr(device, stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def generate_ptr(dist: Distribution, engine: Engine, n: int, dev_ptr: int, stream_ptr: int) -> None:
+    """grng_generate on a raw device address and a raw cudaStream_t value."""
+    d = dist._c()
+    _check(load().grng_generate(ctypes.byref(d), engine.handle, n, ctypes.c_void_p(dev_ptr),
+                                ctypes.c_void_p(stream_ptr)), "grng_generate")
+
+
+def generate(dist: Distribution, engine: Engine, out, n: int | None = None, stream=None):
+    """Fills a CUDA tensor (contiguous, dtype matching dist) and advances the engine.
+
+    out may be a view at any element offset; n defaults to out.numel().
+    Returns out.
+    """
+    import torch
+
+    if not out.is_cuda:
+        raise ValueError("out must be a CUDA tensor")
+    if not out.is_contiguous():
+        raise ValueError("out must be contiguous")
+    if not _torch_dtype_ok(out, dist.dtype):
+        raise ValueError(f"tensor dtype {out.dtype} does not match distribution dtype {dist.dtype}")
+    n = out.numel() if n is None else n
+    if n > out.numel():
+        raise ValueError("n exceeds the tensor size")
+    with torch.cuda.device(out.device):
+        generate_ptr(dist, engine, n, out.data_ptr(), _stream_ptr(out.device, stream))
+    return out
+
+
+def generate_substreams(dist: Distribution, engine: Engine, out, n_per_stream: int,
+                        num_streams: int, stride: int, stream=None):
+    """Substream s fills out[s * n_per_stream : (s + 1) * n_per_stream] from word
+    offset engine.offset + s * stride.  The engine does not advance."""
+    import torch
+
+    if not out.is_cuda or not out.is_contiguous() or not _torch_dtype_ok(out, dist.dtype):
+        raise ValueError("out must be a contiguous CUDA tensor of the distribution's dtype")
+    if n_per_stream * num_streams > out.numel():
+        raise ValueError("out is too small")
+    lo, hi = _split128(stride)
+    d = dist._c()
+    with torch.cuda.device(out.device):
+        _check(load().grng_generate_substreams(ctypes.byref(d), engine.handle, n_per_stream,
+                                               num_streams, lo, hi,
+                                               ctypes.c_void_p(out.data_ptr()),
+                                               ctypes.c_void_p(_stream_ptr(out.device, stream))),
+               "grng_generate_substreams")
+    return out
+
+
+def generate_host(dist: Distribution, engine: Engine, host_out, work, stream=None,
+                  n: int | None = None):
+    """grng_generate_host: fills a CPU tensor through the device buffer `work`
+    (a CUDA tensor of at least 2 MiB).  Synchronous."""
+    import torch
+
+    if host_out.is_cuda or not host_out.is_contiguous() or not _torch_dtype_ok(host_out,
+                                                                                 dist.dtype):
+        raise ValueError("host_out must be a contiguous CPU tensor of the distribution's dtype")
+    n = host_out.numel() if n is None else n
+    d = dist._c()
+    nbytes = work.numel() * work.element_size()
+    with torch.cuda.device(work.device):
+        _check(load().grng_generate_host(ctypes.byref(d), engine.handle, n,
+                                         ctypes.c_void_p(host_out.data_ptr()),
+                                         ctypes.c_void_p(work.data_ptr()), nbytes,
+                                         ctypes.c_void_p(_stream_ptr(work.device, stream))),
+               "grng_generate_host")
+    return host_out

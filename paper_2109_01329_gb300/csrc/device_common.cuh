@@ -1,0 +1,211 @@
+// Device-side building blocks shared by the Philox and MRG32k3a fill kernels:
+// the Philox4x32-10 bijection, exact word -> uniform conversions, the fused
+// range transform and the Box-Muller / lognormal transforms.
+#pragma once
+
+#include <cstdint>
+
+#include "grng_internal.h"
+
+namespace grng {
+namespace dev {
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Per round: the two
+// 32x32 -> 64-bit products of counter words 0 and 2 with fixed multipliers;
+// the high halves are mixed with counter words 1, 3 and the round key, the
+// low halves move to words 1 and 3.  The key advances by two Weyl constants
+// between rounds.  The round keys are warp-uniform, so the compiler keeps
+// them in uniform registers.
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+    const uint32_t lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+    const uint32_t lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return c;
+}
+
+// 128-bit counter from (lo, hi) 64-bit halves.
+__device__ __forceinline__ uint4 ctr_from(uint64_t lo, uint64_t hi) {
+  return make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+}
+
+// (lo, hi) += v with carry.
+__device__ __forceinline__ void add128(uint64_t& lo, uint64_t& hi, uint64_t v) {
+  const uint64_t s = lo + v;
+  hi += (s < lo) ? 1u : 0u;
+  lo = s;
+}
+
+// ------------------------------------------------------------ conversions
+// u = (w >> 8) 2^-24: the 24-bit integer converts exactly, the scale is exact.
+__device__ __forceinline__ float u01_f32(uint32_t w) {
+  return __uint2float_rn(w >> 8) * 0x1p-24f;
+}
+// Box-Muller's first input: ((w >> 8) + 1) 2^-24 in (0, 1].
+__device__ __forceinline__ float u01_open0_f32(uint32_t w) {
+  return __uint2float_rn((w >> 8) + 1u) * 0x1p-24f;
+}
+
+// x 2^e for an integer 0 <= x <= 2^53, built with integer operations only
+// (exact: x has at most 53 significant bits, or is 2^53, and the result is a
+// normal double for the exponents used here).  Avoids the FP64 pipe, which
+// is narrow on this part.
+__device__ __forceinline__ double scaled_u54_to_f64(uint64_t x, int e) {
+  if (x == 0) return 0.0;
+  const int lz = __clzll((long long)x);
+  const int msb = 63 - lz;
+  const uint64_t frac = ((x << lz) << 1) >> 12;  // drop the leading one, keep 52 bits
+  const uint64_t bexp = (uint64_t)(1023 + msb + e);
+  return __longlong_as_double((long long)((bexp << 52) | frac));
+}
+
+// Signed form: v 2^e for |v| <= 2^53.
+__device__ __forceinline__ double scaled_i54_to_f64(int64_t v, int e) {
+  const uint64_t mag = v < 0 ? (uint64_t)(-v) : (uint64_t)v;
+  const double r = scaled_u54_to_f64(mag, e);
+  return v < 0 ? -r : r;
+}
+
+// The 53-bit integer of an FP64 uniform: ((w_a << 32) | w_b) >> 11.
+__device__ __forceinline__ uint64_t u53(uint32_t wa, uint32_t wb) {
+  return ((((uint64_t)wa) << 32) | (uint64_t)wb) >> 11;
+}
+
+// ---------------------------------------------------------- range transform
+// Sec. 3.3, Listing 2 computes acc * (b - a) + a in a second kernel; here it
+// is fused, with explicit round-to-nearest multiply and add (never
+// contracted into an FMA) and the half-open interval enforced.
+__device__ __forceinline__ float range_f32(float u, const TransformParams& t) {
+  const float r = __fadd_rn(t.fa, __fmul_rn(t.fd, u));
+  return r >= t.fb ? t.fbprev : r;
+}
+__device__ __forceinline__ double range_f64(double u, const TransformParams& t) {
+  const double r = __dadd_rn(t.da, __dmul_rn(t.dd, u));
+  return r >= t.db ? t.dbprev : r;
+}
+
+// -------------------------------------------------------------- Box-Muller
+// Accurate single-precision functions (no __ intrinsics): logf, sqrtf
+// (correctly rounded) and sincospif of 2 u2, which is exact.
+__device__ __forceinline__ void box_muller_f32(uint32_t w0, uint32_t w1, float& z0, float& z1) {
+  const float u1 = u01_open0_f32(w0);
+  const float u2 = u01_f32(w1);
+  const float rho = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  z0 = rho * c;
+  z1 = rho * s;
+}
+
+__device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
+                                               double& z0, double& z1) {
+  const double u1 = scaled_u54_to_f64(u53(w0, w1) + 1u, -53);
+  const double two_u2 = scaled_u54_to_f64(u53(w2, w3), -52);
+  const double rho = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincospi(two_u2, &s, &c);
+  z0 = rho * c;
+  z1 = rho * s;
+}
+
+// ------------------------------------------------- one unit -> its outputs
+// Writes the output words (4 bytes each) of one unit from its words.
+template <int V>
+__device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
+                                             const TransformParams& t) {
+  if constexpr (V == V_BITS) {
+    o[0] = w[0];
+  } else if constexpr (V == V_U01_F32) {
+    o[0] = __float_as_uint(u01_f32(w[0]));
+  } else if constexpr (V == V_UNI_F32) {
+    o[0] = __float_as_uint(range_f32(u01_f32(w[0]), t));
+  } else if constexpr (V == V_U01_F64 || V == V_AFF_F64 || V == V_UNI_F64) {
+    double r;
+    if constexpr (V == V_U01_F64) {
+      r = scaled_u54_to_f64(u53(w[0], w[1]), -53);
+    } else if constexpr (V == V_AFF_F64) {
+      r = scaled_i54_to_f64(t.aff_a + (int64_t)u53(w[0], w[1]), t.aff_exp);
+    } else {
+      r = range_f64(scaled_u54_to_f64(u53(w[0], w[1]), -53), t);
+    }
+    const uint64_t b = (uint64_t)__double_as_longlong(r);
+    o[0] = (uint32_t)b;
+    o[1] = (uint32_t)(b >> 32);
+  } else if constexpr (V == V_GAUSS_F32 || V == V_LOGN_F32) {
+    float z0, z1;
+    box_muller_f32(w[0], w[1], z0, z1);
+    float y0 = fmaf(t.fsd, z0, t.fmean);
+    float y1 = fmaf(t.fsd, z1, t.fmean);
+    if constexpr (V == V_LOGN_F32) {
+      y0 = expf(y0);
+      y1 = expf(y1);
+    }
+    o[0] = __float_as_uint(y0);
+    o[1] = __float_as_uint(y1);
+  } else {  // V_GAUSS_F64, V_LOGN_F64
+    double z0, z1;
+    box_muller_f64(w[0], w[1], w[2], w[3], z0, z1);
+    double y0 = fma(t.dsd, z0, t.dmean);
+    double y1 = fma(t.dsd, z1, t.dmean);
+    if constexpr (V == V_LOGN_F64) {
+      y0 = exp(y0);
+      y1 = exp(y1);
+    }
+    const uint64_t b0 = (uint64_t)__double_as_longlong(y0);
+    const uint64_t b1 = (uint64_t)__double_as_longlong(y1);
+    o[0] = (uint32_t)b0;
+    o[1] = (uint32_t)(b0 >> 32);
+    o[2] = (uint32_t)b1;
+    o[3] = (uint32_t)(b1 >> 32);
+  }
+}
+
+// Output words of one 4-word block whose 4 words are exactly the words of
+// 4 / wpu whole units (the aligned case).
+template <int V>
+__device__ __forceinline__ uint4 block_outputs(uint4 b, const TransformParams& t) {
+  constexpr int kWpu = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 1
+                       : (V == V_GAUSS_F64 || V == V_LOGN_F64)          ? 4
+                                                                         : 2;
+  uint32_t w[4] = {b.x, b.y, b.z, b.w};
+  uint32_t o[4];
+#pragma unroll
+  for (int u = 0; u < 4 / kWpu; ++u) unit_outputs<V>(w + u * kWpu, o + u * kWpu, t);
+  return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
+template <int V>
+struct VInfo {
+  static constexpr int wpu = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 1
+                             : (V == V_GAUSS_F64 || V == V_LOGN_F64)          ? 4
+                                                                               : 2;
+  static constexpr int es = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32 ||
+                             V == V_GAUSS_F32 || V == V_LOGN_F32)
+                                ? 4
+                                : 8;
+  static constexpr int epu = (V == V_GAUSS_F32 || V == V_LOGN_F32 || V == V_GAUSS_F64 ||
+                              V == V_LOGN_F64)
+                                 ? 2
+                                 : 1;
+  static constexpr int ow_per_elem = es / 4;  // output words per element
+};
+
+// 16-byte vector store (the address must be 16-byte aligned).
+__device__ __forceinline__ void store16(void* p, uint4 v) {
+  *reinterpret_cast<uint4*>(p) = v;
+}
+
+}  // namespace dev
+}  // namespace grng

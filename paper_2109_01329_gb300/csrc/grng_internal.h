@@ -1,0 +1,83 @@
+// Internal types shared by the host C ABI (capi.cpp) and the kernel launchers
+// (philox_kernels.cu, mrg_kernels.cu).  Not part of the public interface.
+#pragma once
+
+#include <cstdint>
+
+#include "grng.h"
+
+struct CUstream_st;
+
+namespace grng {
+
+// One variant per (distribution, dtype) plus exact fast forms of the uniform
+// transform that give bit-identical results (see TransformParams).
+enum Variant : int {
+  V_BITS = 0,      // uint32 words
+  V_U01_F32 = 1,   // uniform F32 on [0, 1): u itself (0 + 1 * u == u exactly)
+  V_UNI_F32 = 2,   // uniform F32 on [a, b): RN mul, RN add, clamp below b
+  V_U01_F64 = 3,   // uniform F64 on [0, 1)
+  V_AFF_F64 = 4,   // uniform F64 on [a, b) when a + (b - a) u is exact: integer form
+  V_UNI_F64 = 5,   // uniform F64 on [a, b): FP64 RN mul, RN add, clamp
+  V_GAUSS_F32 = 6,
+  V_LOGN_F32 = 7,
+  V_GAUSS_F64 = 8,
+  V_LOGN_F64 = 9,
+  V_COUNT = 10
+};
+
+// Geometry of a variant.  Every variant produces 4 output bytes per word it
+// consumes, so a 16-byte output group always corresponds to 4 words.
+struct VariantInfo {
+  int es;   // element size in bytes
+  int wpu;  // words per unit (a unit is one output, or one Box-Muller pair)
+  int epu;  // elements per unit
+};
+
+inline VariantInfo variant_info(int v) {
+  switch (v) {
+    case V_BITS: case V_U01_F32: case V_UNI_F32: return {4, 1, 1};
+    case V_U01_F64: case V_AFF_F64: case V_UNI_F64: return {8, 2, 1};
+    case V_GAUSS_F32: case V_LOGN_F32: return {4, 2, 2};
+    default: return {8, 4, 2};  // V_GAUSS_F64, V_LOGN_F64
+  }
+}
+
+// Distribution parameters as the kernels use them.
+struct TransformParams {
+  float fa, fd, fb, fbprev;   // F32 uniform: a, b - a, b, largest float below b
+  float fmean, fsd;           // F32 gaussian (mean, sd) / lognormal (m, s)
+  double da, dd, db, dbprev;  // F64 uniform
+  double dmean, dsd;          // F64 gaussian / lognormal
+  int64_t aff_a;              // F64 exact affine: r = (aff_a + x) 2^aff_exp, x = 53-bit word
+  int32_t aff_exp;
+  int32_t pad;
+};
+
+// One fill request as the launchers see it: num_streams streams of n
+// elements; stream s starts at word offset off + s * stride and writes
+// out + s * n elements.
+struct FillRequest {
+  int variant;
+  int engine_kind;
+  int64_t n;
+  int64_t num_streams;
+  uint64_t off_lo, off_hi;
+  uint64_t stride_lo, stride_hi;
+  void* out;
+  TransformParams t;
+  uint32_t key[2];     // Philox key
+  uint32_t mrg[6];     // MRG32k3a state at word offset off: x1[3], x2[3]
+};
+
+// Kernel launchers; return GRNG_OK or GRNG_ERR_CUDA (detail via set_error).
+grng_status launch_philox(const FillRequest& r, CUstream_st* stream);
+grng_status launch_mrg(const FillRequest& r, CUstream_st* stream);
+
+// Records an error message for grng_last_error() on this thread.
+void set_error(const char* fmt, ...);
+
+// Multiprocessor count of the current device (cached per device).
+int current_device_sms(int* device_out);
+
+}  // namespace grng

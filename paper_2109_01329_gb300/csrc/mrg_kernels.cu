@@ -1,0 +1,281 @@
+// MRG32k3a fill kernels with the distribution transform fused in.
+//
+// MRG32k3a (L'Ecuyer 1999; the paper's "MRG-based generators", Sec. 3.1) is a
+// sequential recursion, so the output is cut into per-thread chunks of
+// consecutive units.  Each thread
+//   1. jumps the call's starting state to its chunk with the compile-time
+//      table of A^(2^j) in constant memory (all lanes read the same level at
+//      the same time, so the reads broadcast);
+//   2. steps the two component recursions in registers, with products
+//      reduced by folding 2^32 = c (mod 2^32 - c) instead of dividing;
+//   3. transforms each unit and writes its output words to its row of a
+//      per-warp shared-memory stage (rows padded to 33 words: no bank
+//      conflicts);
+//   4. with its warp, copies the 32 staged rows out: 8 lanes per 128-byte
+//      row with 16-byte stores when the output is 16-byte aligned, otherwise
+//      one 128-byte row per instruction with 4-byte stores.
+// Chunks are placed so that every chunk starts on a 16-byte output boundary
+// (the first chunk of a stream has virtual head units), hence aligned rows.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "grng_internal.h"
+#include "mrg_tables.h"
+
+namespace grng {
+
+__constant__ mrg::PowTable c_mrg_pow = mrg::make_pow_table();
+
+namespace {
+
+using namespace dev;
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kRowWords = 32;  // output words per row per sub-chunk (128 bytes)
+
+struct MrgParams {
+  TransformParams t;
+  void* out;
+  int64_t n;                  // elements per stream
+  int64_t units;              // units per stream
+  int64_t out_words;          // output words per stream (n * es / 4)
+  int64_t chunk_units;        // units per thread (multiple of 32 / wpu)
+  int64_t chunks_per_stream;
+  int64_t total_chunks;
+  int64_t head_units;         // virtual units before `out` in the first chunk
+  uint64_t stride_lo, stride_hi;  // word stride between streams
+  uint32_t x[6];              // state at the call's word offset
+};
+
+__device__ __forceinline__ uint32_t red_m1(uint64_t p) {
+  // p < 2^54: two folds of 2^32 = 209 (mod m1), then one conditional subtract
+  uint64_t t = (p & 0xFFFFFFFFull) + (p >> 32) * (uint64_t)mrg::C1;
+  t = (t & 0xFFFFFFFFull) + (t >> 32) * (uint64_t)mrg::C1;
+  return (uint32_t)(t >= mrg::M1 ? t - mrg::M1 : t);
+}
+__device__ __forceinline__ uint32_t red_m2(uint64_t p) {
+  uint64_t t = (p & 0xFFFFFFFFull) + (p >> 32) * (uint64_t)mrg::C2;
+  t = (t & 0xFFFFFFFFull) + (t >> 32) * (uint64_t)mrg::C2;
+  return (uint32_t)(t >= mrg::M2 ? t - mrg::M2 : t);
+}
+
+struct MrgRegs {
+  uint32_t a0, a1, a2;  // x1_{n-3}, x1_{n-2}, x1_{n-1}
+  uint32_t b0, b1, b2;  // x2_{n-3}, x2_{n-2}, x2_{n-1}
+};
+
+// One step of both components; returns z_n = (x1_n - x2_n) mod m1.
+// -a13 x = a13 (m1 - x) (mod m1) keeps the sums non-negative and below 2^54.
+__device__ __forceinline__ uint32_t mrg_next(MrgRegs& s) {
+  const uint64_t p1 = (uint64_t)mrg::A12 * s.a1 + (uint64_t)mrg::A13 * (mrg::M1 - s.a0);
+  const uint64_t p2 = (uint64_t)mrg::A21 * s.b2 + (uint64_t)mrg::A23 * (mrg::M2 - s.b0);
+  const uint32_t n1 = red_m1(p1);
+  const uint32_t n2 = red_m2(p2);
+  s.a0 = s.a1;
+  s.a1 = s.a2;
+  s.a2 = n1;
+  s.b0 = s.b1;
+  s.b1 = s.b2;
+  s.b2 = n2;
+  return n1 >= n2 ? n1 - n2 : n1 - n2 + mrg::M1;
+}
+
+__device__ __forceinline__ void jump(MrgRegs& s, uint64_t e_lo, uint64_t e_hi) {
+  uint32_t x1[3] = {s.a0, s.a1, s.a2};
+  uint32_t x2[3] = {s.b0, s.b1, s.b2};
+  // Uniform loop over levels so that all lanes read the same table entry.
+  for (int j = 0; j < mrg::kLevels; ++j) {
+    const uint64_t word = j < 64 ? e_lo : e_hi;
+    const bool bit = (word >> (j & 63)) & 1u;
+    if (bit) {
+      mrg::matvec(c_mrg_pow.m[0][j], x1, mrg::M1, mrg::C1);
+      mrg::matvec(c_mrg_pow.m[1][j], x2, mrg::M2, mrg::C2);
+    }
+    // stop once no lane has bits left at or above j + 1
+    const uint64_t rest_lo = j + 1 < 64 ? (e_lo >> (j + 1)) : 0;
+    const uint64_t rest_hi = j + 1 < 64 ? e_hi : (j + 1 < 128 ? (e_hi >> ((j + 1) & 63)) : 0);
+    if (!__any_sync(0xFFFFFFFFu, (rest_lo | rest_hi) != 0)) break;
+  }
+  s.a0 = x1[0]; s.a1 = x1[1]; s.a2 = x1[2];
+  s.b0 = x2[0]; s.b1 = x2[1]; s.b2 = x2[2];
+}
+
+template <int V>
+__device__ __forceinline__ void gen_unit(MrgRegs& st, uint32_t* row, int pos,
+                                         const TransformParams& t) {
+  constexpr int kWpu = VInfo<V>::wpu;
+  uint32_t w[kWpu];
+#pragma unroll
+  for (int i = 0; i < kWpu; ++i) w[i] = mrg_next(st);
+  uint32_t o[kWpu];
+  unit_outputs<V>(w, o, t);
+#pragma unroll
+  for (int i = 0; i < kWpu; ++i) row[pos + i] = o[i];
+}
+
+template <int V, bool kAligned>
+__global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
+  constexpr int kWpu = VInfo<V>::wpu;
+  constexpr int kSu = kRowWords / kWpu;  // units per sub-chunk
+  __shared__ uint32_t stage[kWarps][32][kRowWords + 1];
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t cid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const bool active = cid < p.total_chunks;
+  int64_t s = 0, c = 0;
+  if (active) {
+    s = cid / p.chunks_per_stream;
+    c = cid - s * p.chunks_per_stream;
+  }
+  const int64_t u_first = c * p.chunk_units - p.head_units;
+
+  MrgRegs st;
+  st.a0 = p.x[0]; st.a1 = p.x[1]; st.a2 = p.x[2];
+  st.b0 = p.x[3]; st.b1 = p.x[4]; st.b2 = p.x[5];
+  {
+    // words to skip: s * stride + max(u_first, 0) * wpu  (mod 2^128)
+    uint64_t e_lo = 0, e_hi = 0;
+    if (active) {
+      const uint64_t us = (uint64_t)s;
+      e_lo = us * p.stride_lo;
+      e_hi = __umul64hi(us, p.stride_lo) + us * p.stride_hi;
+      const uint64_t add = (uint64_t)((u_first > 0 ? u_first : 0) * kWpu);
+      const uint64_t sum = e_lo + add;
+      e_hi += (sum < e_lo) ? 1u : 0u;
+      e_lo = sum;
+    }
+    jump(st, e_lo, e_hi);
+  }
+
+  uint32_t* row = &stage[warp][lane][0];
+  const int64_t nsub = p.chunk_units / kSu;
+  char* out_base = reinterpret_cast<char*>(p.out);
+  for (int64_t q = 0; q < nsub; ++q) {
+    const int64_t ub = u_first + q * kSu;  // first unit of this sub-chunk
+    if (active) {
+      if (ub >= 0 && ub + kSu <= p.units) {
+#pragma unroll
+        for (int u = 0; u < kSu; ++u) gen_unit<V>(st, row, u * kWpu, p.t);
+      } else {
+        for (int u = 0; u < kSu; ++u) {
+          const int64_t unit = ub + u;
+          if (unit >= 0 && unit < p.units) gen_unit<V>(st, row, u * kWpu, p.t);
+        }
+      }
+    }
+    __syncwarp();
+    const uint32_t s_lo = (uint32_t)s, s_hi = (uint32_t)((uint64_t)s >> 32);
+    const uint32_t ub_lo = (uint32_t)ub, ub_hi = (uint32_t)((uint64_t)ub >> 32);
+    if constexpr (kAligned) {
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int r = it * 4 + (lane >> 3);
+        const int piece = lane & 7;
+        const bool r_active = __shfl_sync(0xFFFFFFFFu, active ? 1 : 0, r) != 0;
+        const int64_t r_s = (int64_t)(((uint64_t)__shfl_sync(0xFFFFFFFFu, s_hi, r) << 32) |
+                                      __shfl_sync(0xFFFFFFFFu, s_lo, r));
+        const int64_t r_ub = (int64_t)(((uint64_t)__shfl_sync(0xFFFFFFFFu, ub_hi, r) << 32) |
+                                       __shfl_sync(0xFFFFFFFFu, ub_lo, r));
+        if (!r_active) continue;
+        const int64_t ow = r_ub * kWpu + piece * 4;  // output word within the stream
+        uint32_t* dst = reinterpret_cast<uint32_t*>(out_base) + r_s * p.out_words + ow;
+        const uint32_t* src = &stage[warp][r][piece * 4];
+        if (ow >= 0 && ow + 4 <= p.out_words) {
+          store16(dst, make_uint4(src[0], src[1], src[2], src[3]));
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (ow + i >= 0 && ow + i < p.out_words) dst[i] = src[i];
+        }
+      }
+    } else {
+      for (int r = 0; r < 32; ++r) {
+        const bool r_active = __shfl_sync(0xFFFFFFFFu, active ? 1 : 0, r) != 0;
+        const int64_t r_s = (int64_t)(((uint64_t)__shfl_sync(0xFFFFFFFFu, s_hi, r) << 32) |
+                                      __shfl_sync(0xFFFFFFFFu, s_lo, r));
+        const int64_t r_ub = (int64_t)(((uint64_t)__shfl_sync(0xFFFFFFFFu, ub_hi, r) << 32) |
+                                       __shfl_sync(0xFFFFFFFFu, ub_lo, r));
+        if (!r_active) continue;
+        const int64_t ow = r_ub * kWpu + lane;
+        if (ow >= 0 && ow < p.out_words)
+          reinterpret_cast<uint32_t*>(out_base)[r_s * p.out_words + ow] = stage[warp][r][lane];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int V>
+grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
+  using I = VInfo<V>;
+  constexpr int kSu = kRowWords / I::wpu;
+  int dev = 0;
+  const int sms = current_device_sms(&dev);
+  MrgParams p;
+  p.t = r.t;
+  p.out = r.out;
+  p.n = r.n;
+  p.units = (r.n + I::epu - 1) / I::epu;
+  p.out_words = r.n * (I::es / 4);
+  p.stride_lo = r.stride_lo;
+  p.stride_hi = r.stride_hi;
+  for (int i = 0; i < 6; ++i) p.x[i] = r.mrg[i];
+
+  const uintptr_t addr = (uintptr_t)r.out;
+  const uint32_t phase_w = (uint32_t)((addr & 15u) / 4u);
+  const uint64_t stream_bytes = (uint64_t)r.n * I::es;
+  const bool aligned = (r.num_streams == 1 || (stream_bytes % 16u) == 0) &&
+                       (phase_w % (uint32_t)I::wpu) == 0;
+  p.head_units = aligned ? (int64_t)(phase_w / I::wpu) : 0;
+
+  // About one resident wave of threads, one chunk each.
+  const int64_t target_threads = (int64_t)sms * 2048;
+  int64_t per_stream_threads = target_threads / r.num_streams;
+  if (per_stream_threads < 1) per_stream_threads = 1;
+  const int64_t span = p.units + p.head_units;
+  int64_t cu = (span + per_stream_threads - 1) / per_stream_threads;
+  if (cu < 2 * kSu) cu = 2 * kSu;
+  cu = (cu + kSu - 1) / kSu * kSu;
+  p.chunk_units = cu;
+  p.chunks_per_stream = (span + cu - 1) / cu;
+  p.total_chunks = p.chunks_per_stream * r.num_streams;
+  const int64_t grid = (p.total_chunks + kThreads - 1) / kThreads;
+  if (grid > 0x7FFFFFFF) {
+    set_error("MRG32k3a fill: grid too large");
+    return GRNG_ERR_UNSUPPORTED;
+  }
+  if (aligned) {
+    mrg_fill_kernel<V, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+  } else {
+    mrg_fill_kernel<V, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+  }
+  const cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    set_error("MRG32k3a fill launch failed: %s", cudaGetErrorString(err));
+    return GRNG_ERR_CUDA;
+  }
+  return GRNG_OK;
+}
+
+}  // namespace
+
+grng_status launch_mrg(const FillRequest& r, CUstream_st* stream) {
+  switch (r.variant) {
+    case V_BITS: return launch_variant<V_BITS>(r, stream);
+    case V_U01_F32: return launch_variant<V_U01_F32>(r, stream);
+    case V_UNI_F32: return launch_variant<V_UNI_F32>(r, stream);
+    case V_U01_F64: return launch_variant<V_U01_F64>(r, stream);
+    case V_AFF_F64: return launch_variant<V_AFF_F64>(r, stream);
+    case V_UNI_F64: return launch_variant<V_UNI_F64>(r, stream);
+    case V_GAUSS_F32: return launch_variant<V_GAUSS_F32>(r, stream);
+    case V_LOGN_F32: return launch_variant<V_LOGN_F32>(r, stream);
+    case V_GAUSS_F64: return launch_variant<V_GAUSS_F64>(r, stream);
+    case V_LOGN_F64: return launch_variant<V_LOGN_F64>(r, stream);
+    default: set_error("unknown variant %d", r.variant); return GRNG_ERR_INVALID_ARG;
+  }
+}
+
+}  // namespace grng

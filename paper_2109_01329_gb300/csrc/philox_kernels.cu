@@ -1,0 +1,324 @@
+// Philox4x32-10 fill kernels with the distribution transform fused in.
+//
+// The paper's path is two kernels: the vendor generator writes raw uniforms,
+// then a SYCL kernel re-reads and rewrites the buffer to apply the range
+// (Sec. 3.3, Listings 1 and 2; profiled as separate kernels in Sec. 6, Fig. 4).
+// Here one kernel computes each counter block in registers, transforms it and
+// stores it once: 4 output bytes per word and no reads.
+//
+// Output is cut into 16-byte groups at 16-byte aligned addresses.  Every
+// variant consumes exactly 4 words per 16 output bytes, so:
+//   * fast kernel: when the word phase of the first group matches its block
+//     boundary (and Box-Muller pairs do not straddle groups), group j is
+//     exactly Philox block base + j: one block, one transform, one st.v4.
+//     Only the first and the last group may be partial.
+//   * staged kernel: any other phase.  A CTA computes the blocks covering a
+//     tile of 256 groups into shared memory, then each thread assembles its
+//     group from the words it needs.
+// Both write every output exactly once; results do not depend on the launch
+// geometry (each output is a function of its word index only).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "grng_internal.h"
+
+namespace grng {
+namespace {
+
+using namespace dev;
+
+constexpr int kThreads = 256;
+
+struct FastParams {
+  TransformParams t;
+  void* out;
+  int64_t n;          // elements per stream
+  int64_t groups;     // 16-byte groups per stream
+  int64_t total;      // groups * num_streams
+  int64_t head;       // elements of group 0 that lie before `out`
+  uint64_t base_lo;   // block counter of group 0 of stream 0
+  uint64_t base_hi;
+  uint64_t sb_lo;     // block-counter stride between streams
+  uint64_t sb_hi;
+  int64_t tq;         // grid stride = tq * groups + tr (multi-stream walk)
+  int64_t tr;
+  uint64_t tqsb_lo;   // tq * sb
+  uint64_t tqsb_hi;
+  uint32_t k0, k1;
+};
+
+__device__ __forceinline__ void add128(uint64_t& lo, uint64_t& hi, uint64_t vlo, uint64_t vhi) {
+  const uint64_t s = lo + vlo;
+  hi += vhi + ((s < lo) ? 1u : 0u);
+  lo = s;
+}
+
+// Stores the in-range elements of a partial group.
+template <int V>
+__device__ __forceinline__ void store_partial(char* stream_base, int64_t e0, int64_t n, uint4 o) {
+  using I = VInfo<V>;
+  constexpr int kEpg = 16 / I::es;
+  const uint32_t ow[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+  for (int i = 0; i < kEpg; ++i) {
+    const int64_t e = e0 + i;
+    if (e >= 0 && e < n) {
+      if constexpr (I::es == 4) {
+        reinterpret_cast<uint32_t*>(stream_base)[e] = ow[i];
+      } else {
+        reinterpret_cast<uint2*>(stream_base)[e] = make_uint2(ow[2 * i], ow[2 * i + 1]);
+      }
+    }
+  }
+}
+
+template <int V, bool kMulti>
+__global__ void __launch_bounds__(kThreads) philox_fast_kernel(const FastParams p) {
+  using I = VInfo<V>;
+  constexpr int kEpg = 16 / I::es;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (idx >= p.total) return;
+
+  int64_t s = 0;
+  int64_t j = idx;
+  uint64_t sb_lo = p.base_lo, sb_hi = p.base_hi;  // block counter of group 0 of stream s
+  if constexpr (kMulti) {
+    s = idx / p.groups;
+    j = idx - s * p.groups;
+    // sb += s * (sb_lo, sb_hi)
+    const uint64_t us = (uint64_t)s;
+    add128(sb_lo, sb_hi, us * p.sb_lo, __umul64hi(us, p.sb_lo) + us * p.sb_hi);
+  }
+  for (; idx < p.total; idx += stride) {
+    uint64_t c_lo = sb_lo, c_hi = sb_hi;
+    add128(c_lo, c_hi, (uint64_t)j, 0);
+    const uint4 blk = philox4x32_10(ctr_from(c_lo, c_hi), p.k0, p.k1);
+    const uint4 o = block_outputs<V>(blk, p.t);
+    char* sbase = reinterpret_cast<char*>(p.out) + (s * p.n) * I::es;
+    const int64_t e0 = j * kEpg - p.head;
+    if (e0 >= 0 && e0 + kEpg <= p.n) {
+      store16(sbase + e0 * I::es, o);
+    } else {
+      store_partial<V>(sbase, e0, p.n, o);
+    }
+    if constexpr (kMulti) {
+      j += p.tr;
+      s += p.tq;
+      add128(sb_lo, sb_hi, p.tqsb_lo, p.tqsb_hi);
+      if (j >= p.groups) {
+        j -= p.groups;
+        s += 1;
+        add128(sb_lo, sb_hi, p.sb_lo, p.sb_hi);
+      }
+    } else {
+      j += stride;
+    }
+  }
+}
+
+struct StagedParams {
+  TransformParams t;
+  void* out;
+  int64_t n;                 // elements per stream
+  int64_t num_streams;
+  int64_t tiles_per_stream;  // tiles of kThreads groups
+  uint64_t off_lo, off_hi;   // word offset of stream 0
+  uint64_t stride_lo, stride_hi;
+  uint32_t k0, k1;
+};
+
+// Blocks per tile: 256 groups are 1024 words, plus up to 3 words of a unit
+// straddling each end, plus block rounding.
+constexpr int kTileBlocks = kThreads + 4;
+
+template <int V>
+__global__ void __launch_bounds__(kThreads) philox_staged_kernel(const StagedParams p) {
+  using I = VInfo<V>;
+  constexpr int kEpg = 16 / I::es;
+  constexpr int kWpu = I::wpu;
+  constexpr int kEpu = I::epu;
+  constexpr int kOwpe = I::ow_per_elem;
+  __shared__ uint4 sblocks[kTileBlocks];
+  const uint32_t* swords = reinterpret_cast<const uint32_t*>(sblocks);
+
+  const int64_t total_tiles = p.num_streams * p.tiles_per_stream;
+  for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+    const int64_t s = tile / p.tiles_per_stream;
+    const int64_t q = tile - s * p.tiles_per_stream;
+    char* sbase = reinterpret_cast<char*>(p.out) + (s * p.n) * I::es;
+    const int64_t head = (int64_t)(((uintptr_t)sbase & 15u) / I::es);
+    // elements of this tile, clipped to [0, n)
+    const int64_t te0 = q * kThreads * kEpg - head;
+    const int64_t lo_e = te0 < 0 ? 0 : te0;
+    const int64_t hi_e = (te0 + kThreads * kEpg) < p.n ? (te0 + kThreads * kEpg) : p.n;
+    if (lo_e >= hi_e) continue;  // uniform across the CTA
+    const int64_t k_lo = lo_e / kEpu;
+    const int64_t k_hi = (hi_e - 1) / kEpu;
+    // first word of unit k_lo: W = off + s * stride + k_lo * wpu (128-bit)
+    uint64_t w_lo = p.off_lo, w_hi = p.off_hi;
+    {
+      const uint64_t us = (uint64_t)s;
+      add128(w_lo, w_hi, us * p.stride_lo, __umul64hi(us, p.stride_lo) + us * p.stride_hi);
+      add128(w_lo, w_hi, (uint64_t)(k_lo * kWpu), 0);
+    }
+    const uint32_t wphase = (uint32_t)(w_lo & 3u);
+    // block counter of the first word
+    const uint64_t b_lo = (w_lo >> 2) | (w_hi << 62);
+    const uint64_t b_hi = w_hi >> 2;
+    const int64_t nwords = (k_hi - k_lo + 1) * kWpu;
+    const int nblocks = (int)((wphase + nwords + 3) >> 2);
+    for (int i = threadIdx.x; i < nblocks; i += kThreads) {
+      uint64_t c_lo = b_lo, c_hi = b_hi;
+      add128(c_lo, c_hi, (uint64_t)i, 0);
+      sblocks[i] = philox4x32_10(ctr_from(c_lo, c_hi), p.k0, p.k1);
+    }
+    __syncthreads();
+
+    const int64_t e0 = te0 + (int64_t)threadIdx.x * kEpg;
+    const int64_t ge_lo = e0 < 0 ? 0 : e0;
+    const int64_t ge_hi = (e0 + kEpg) < p.n ? (e0 + kEpg) : p.n;
+    if (ge_lo < ge_hi) {
+      uint32_t gout[4] = {0u, 0u, 0u, 0u};
+      const int64_t ku_lo = ge_lo / kEpu;
+      const int64_t ku_hi = (ge_hi - 1) / kEpu;
+      for (int64_t k = ku_lo; k <= ku_hi; ++k) {
+        const int64_t rel = (int64_t)wphase + (k - k_lo) * kWpu;
+        uint32_t w[kWpu];
+#pragma unroll
+        for (int i = 0; i < kWpu; ++i) w[i] = swords[rel + i];
+        uint32_t o[kWpu];
+        unit_outputs<V>(w, o, p.t);
+#pragma unroll
+        for (int sl = 0; sl < kEpu; ++sl) {
+          const int64_t e = k * kEpu + sl;
+          if (e >= e0 && e < e0 + kEpg) {
+            const int pos = (int)(e - e0) * kOwpe;
+#pragma unroll
+            for (int i = 0; i < kOwpe; ++i) gout[pos + i] = o[sl * kOwpe + i];
+          }
+        }
+      }
+      const uint4 ov = make_uint4(gout[0], gout[1], gout[2], gout[3]);
+      if (ge_lo == e0 && ge_hi == e0 + kEpg) {
+        store16(sbase + e0 * I::es, ov);
+      } else {
+        store_partial<V>(sbase, e0, p.n, ov);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename K>
+int blocks_per_sm(K kernel) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kThreads, 0) != cudaSuccess ||
+      b < 1) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return b;
+}
+
+template <int V>
+grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
+  using I = VInfo<V>;
+  constexpr int kEpg = 16 / I::es;
+  int dev = 0;
+  const int sms = current_device_sms(&dev);
+  const uintptr_t addr = (uintptr_t)r.out;
+  const uint32_t phase_w = (uint32_t)((addr & 15u) / 4u);  // output words before out in group 0
+  const uint64_t stream_bytes = (uint64_t)r.n * I::es;
+  // same alignment phase for every stream, and a block-multiple stride
+  const bool uniform_streams =
+      r.num_streams == 1 || ((stream_bytes % 16u) == 0 && (r.stride_lo & 3u) == 0);
+  const bool fast = uniform_streams && ((r.off_lo - phase_w) & 3u) == 0 &&
+                    (phase_w % (uint32_t)I::wpu) == 0;
+
+  if (fast) {
+    FastParams p;
+    p.t = r.t;
+    p.out = r.out;
+    p.n = r.n;
+    p.head = (int64_t)(phase_w * 4u / I::es);
+    p.groups = (p.head + r.n + kEpg - 1) / kEpg;
+    p.total = p.groups * r.num_streams;
+    // base block counter = (off - phase_w) / 4 with a 128-bit borrow
+    uint64_t lo = r.off_lo - phase_w;
+    uint64_t hi = r.off_hi - ((r.off_lo < phase_w) ? 1u : 0u);
+    p.base_lo = (lo >> 2) | (hi << 62);
+    p.base_hi = hi >> 2;
+    p.sb_lo = (r.stride_lo >> 2) | (r.stride_hi << 62);
+    p.sb_hi = r.stride_hi >> 2;
+    p.k0 = r.key[0];
+    p.k1 = r.key[1];
+    const bool multi = r.num_streams > 1;
+    auto kernel = multi ? philox_fast_kernel<V, true> : philox_fast_kernel<V, false>;
+    static int occ[2] = {0, 0};
+    int& o = occ[multi ? 1 : 0];
+    if (o == 0) o = blocks_per_sm(kernel);
+    int64_t grid = (p.total + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)sms * o;
+    if (grid > cap) grid = cap;
+    const int64_t gstride = grid * kThreads;
+    p.tq = gstride / p.groups;
+    p.tr = gstride - p.tq * p.groups;
+    // tq * sb (tq < 2^31)
+    const unsigned __int128 tqsb =
+        (unsigned __int128)(uint64_t)p.tq *
+        (((unsigned __int128)p.sb_hi << 64) | (unsigned __int128)p.sb_lo);
+    p.tqsb_lo = (uint64_t)tqsb;
+    p.tqsb_hi = (uint64_t)(tqsb >> 64);
+    kernel<<<(unsigned)grid, kThreads, 0, stream>>>(p);
+  } else {
+    StagedParams p;
+    p.t = r.t;
+    p.out = r.out;
+    p.n = r.n;
+    p.num_streams = r.num_streams;
+    // at most 16 / es - 1 head elements per stream
+    const int64_t max_groups = (r.n + (kEpg - 1) + kEpg - 1) / kEpg;
+    p.tiles_per_stream = (max_groups + kThreads - 1) / kThreads;
+    p.off_lo = r.off_lo;
+    p.off_hi = r.off_hi;
+    p.stride_lo = r.stride_lo;
+    p.stride_hi = r.stride_hi;
+    p.k0 = r.key[0];
+    p.k1 = r.key[1];
+    static int occ = 0;
+    if (occ == 0) occ = blocks_per_sm(philox_staged_kernel<V>);
+    int64_t grid = p.num_streams * p.tiles_per_stream;
+    const int64_t cap = (int64_t)sms * occ;
+    if (grid > cap) grid = cap;
+    philox_staged_kernel<V><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+  }
+  const cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    set_error("Philox fill launch failed: %s", cudaGetErrorString(err));
+    return GRNG_ERR_CUDA;
+  }
+  return GRNG_OK;
+}
+
+}  // namespace
+
+grng_status launch_philox(const FillRequest& r, CUstream_st* stream) {
+  switch (r.variant) {
+    case V_BITS: return launch_variant<V_BITS>(r, stream);
+    case V_U01_F32: return launch_variant<V_U01_F32>(r, stream);
+    case V_UNI_F32: return launch_variant<V_UNI_F32>(r, stream);
+    case V_U01_F64: return launch_variant<V_U01_F64>(r, stream);
+    case V_AFF_F64: return launch_variant<V_AFF_F64>(r, stream);
+    case V_UNI_F64: return launch_variant<V_UNI_F64>(r, stream);
+    case V_GAUSS_F32: return launch_variant<V_GAUSS_F32>(r, stream);
+    case V_LOGN_F32: return launch_variant<V_LOGN_F32>(r, stream);
+    case V_GAUSS_F64: return launch_variant<V_GAUSS_F64>(r, stream);
+    case V_LOGN_F64: return launch_variant<V_LOGN_F64>(r, stream);
+    default: set_error("unknown variant %d", r.variant); return GRNG_ERR_INVALID_ARG;
+  }
+}
+
+}  // namespace grng

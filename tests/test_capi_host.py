@@ -1,0 +1,140 @@
+"""The C ABI without a GPU: the library loads, exports every function that
+include/grng.h declares, and its host-side logic (engines, offsets, the
+consumption rule, argument checks) behaves as documented.  No call here
+reaches a kernel launch."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def g():
+    import __graft_entry__  # noqa: F401  (build helper lives there)
+    from paper_2109_01329_gb300 import build
+
+    build.build()
+    import paper_2109_01329_gb300 as grng
+
+    grng.load()
+    return grng
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "grng.h")).read()
+    return sorted(set(re.findall(r"GRNG_API\s+[\w\s\*]+?\b(grng_\w+)\s*\(", src)))
+
+
+def test_header_declares_expected_functions():
+    decl = _declared_functions()
+    assert "grng_generate" in decl and "grng_engine_create" in decl
+    assert len(decl) >= 12
+
+
+def test_library_exports_every_declared_function(g):
+    lib = g.load()
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(g.EXPORTED) == sorted(_declared_functions())
+
+
+def test_status_strings(g):
+    lib = g.load()
+    assert lib.grng_status_string(0) == b"GRNG_OK"
+    assert lib.grng_status_string(4) == b"GRNG_ERR_CUDA"
+    assert lib.grng_status_string(99) == b"GRNG_ERR_UNKNOWN"
+
+
+@pytest.mark.parametrize("dist,n", [((0, 0), 7), ((1, 1), 5), ((1, 2), 5), ((2, 1), 5),
+                                    ((2, 2), 5), ((3, 1), 1), ((3, 2), 2), ((2, 1), 0)])
+def test_words_for_matches_oracle(g, dist, n):
+    kind, dtype = dist
+    d = g.Distribution(kind, dtype, 0.0, 1.0)
+    assert g.words_for(d, n) == oracle.words_for(kind, dtype, n)
+
+
+def test_engine_state_offsets_and_skip(g):
+    e = g.Engine(g.PHILOX4X32X10, 2021, 17)
+    assert e.state == (g.PHILOX4X32X10, 2021, 17)
+    e.skip_ahead(2**76 + 3)
+    assert e.offset == 17 + 2**76 + 3
+    e.skip_ahead(2**128 - 1)  # wraps mod 2^128
+    assert e.offset == 17 + 2**76 + 2
+    c = e.copy()
+    c.skip_ahead(1)
+    assert c.offset == e.offset + 1
+    r = g.Engine.restore((g.MRG32K3A, 5, 2**100))
+    assert r.state == (g.MRG32K3A, 5, 2**100)
+
+
+def test_zero_size_is_noop_and_keeps_offset(g):
+    e = g.Engine(g.MRG32K3A, 1, 8)
+    g.generate_ptr(g.Distribution.uniform(), e, 0, 0, 0)
+    assert e.offset == 8
+
+
+@pytest.mark.parametrize("dist", [
+    (0, 1, 0.0, 1.0),      # bits with F32
+    (1, 0, 0.0, 1.0),      # uniform with U32
+    (1, 1, 1.0, 1.0),      # a == b
+    (1, 1, 2.0, 1.0),      # a > b
+    (1, 1, -3.5e38, 3.5e38),  # b - a overflows float
+    (1, 2, float("nan"), 1.0),
+    (2, 1, 0.0, 0.0),      # stddev 0
+    (2, 2, 0.0, -1.0),
+    (3, 1, 0.0, float("inf")),
+    (7, 1, 0.0, 1.0),      # unknown kind
+])
+def test_invalid_distributions_rejected_engine_unchanged(g, dist):
+    e = g.Engine(g.PHILOX4X32X10, 3, 0)
+    with pytest.raises(g.GrngError) as ei:
+        g.generate_ptr(g.Distribution(*dist), e, 16, 0x100000, 0)
+    assert ei.value.status == 1
+    assert e.offset == 0
+
+
+def test_invalid_pointer_and_size(g):
+    e = g.Engine(g.PHILOX4X32X10, 3, 0)
+    with pytest.raises(g.GrngError):  # NULL with n > 0
+        g.generate_ptr(g.Distribution.uniform(), e, 4, 0, 0)
+    with pytest.raises(g.GrngError):  # F32 pointer not 4-byte aligned
+        g.generate_ptr(g.Distribution.uniform(), e, 4, 0x100002, 0)
+    with pytest.raises(g.GrngError):  # F64 pointer not 8-byte aligned
+        g.generate_ptr(g.Distribution.uniform(dtype=g.F64), e, 4, 0x100004, 0)
+    with pytest.raises(g.GrngError):
+        g.generate_ptr(g.Distribution.uniform(), e, -1, 0x100000, 0)
+    with pytest.raises(g.GrngError) as ei:
+        g.generate_ptr(g.Distribution.uniform(), e, (1 << 40) + 1, 0x100000, 0)
+    assert ei.value.status == 2
+    assert e.offset == 0
+
+
+def test_null_engine_and_create_errors(g):
+    lib = g.load()
+    d = g.Distribution.uniform()._c()
+    assert lib.grng_generate(ctypes.byref(d), None, 4, ctypes.c_void_p(0x1000), None) == 1
+    h = ctypes.c_void_p()
+    assert lib.grng_engine_create(ctypes.byref(h), 9, 1, 0) == 1
+    assert lib.grng_engine_create(None, 0, 1, 0) == 1
+    assert lib.grng_engine_destroy(None) == 0
+    assert lib.grng_words_for(None, 4, None) == 1
+
+
+def test_substream_limits(g):
+    lib = g.load()
+    e = g.Engine(g.MRG32K3A, 1, 0)
+    d = g.Distribution.gaussian(dtype=g.F64)._c()
+    st = lib.grng_generate_substreams(ctypes.byref(d), e.handle, 1 << 30, 1 << 20, 0, 1 << 12,
+                                      ctypes.c_void_p(0x1000), None)
+    assert st == 2
+    st = lib.grng_generate_substreams(ctypes.byref(d), e.handle, 0, 5, 0, 1,
+                                      ctypes.c_void_p(0), None)
+    assert st == 0
+    assert e.offset == 0
