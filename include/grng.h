@@ -30,7 +30,10 @@
  * (seed mod 2^32, seed >> 32); word g is lane (g mod 4) of the block whose
  * 128-bit counter is floor(g / 4).  MRG32k3a (L'Ecuyer 1999): seeded state
  * x1 = (1, 1, seed mod m1), x2 = (1, 1, 1); word n is (x1_n - x2_n) mod m1.
- * The paper names both engines (Sec. 3.1) but defines neither.
+ * The paper names both engines (Sec. 3.1) but defines neither.  Offsets
+ * are taken mod 2^128: for Philox word 2^128 + g is word g; an MRG32k3a fill
+ * whose words cross 2^128 within one call continues its recursion, and the
+ * engine's next offset is reduced mod 2^128.
  *
  * Words per output (the consumption rule; the paper does not fix one):
  *   bits U32: 1 | uniform F32: 1 | uniform F64: 2 (the earlier word is the

@@ -64,11 +64,23 @@ void init_engine(grng_engine* e, int32_t kind, uint64_t seed, uint64_t off_lo, u
   }
 }
 
+// Offsets are taken mod 2^128.  The cached MRG32k3a state is always the
+// state at that reduced offset: an advance that wraps recomputes it from the
+// seed (within one call a fill that crosses 2^128 continues the recursion).
 void advance_engine(grng_engine* e, uint64_t n_lo, uint64_t n_hi) {
   const uint64_t lo = e->off_lo + n_lo;
-  e->off_hi += n_hi + ((lo < e->off_lo) ? 1u : 0u);
+  const uint64_t c0 = (lo < e->off_lo) ? 1u : 0u;
+  const uint64_t hi1 = e->off_hi + n_hi;
+  const bool wrapped = hi1 < e->off_hi || (hi1 + c0) < hi1;
+  e->off_hi = hi1 + c0;
   e->off_lo = lo;
-  if (e->kind == GRNG_MRG32K3A) mrg_jump_host(e->mrg, n_lo, n_hi);
+  if (e->kind == GRNG_MRG32K3A) {
+    if (wrapped) {
+      init_engine(e, e->kind, e->seed, e->off_lo, e->off_hi);
+    } else {
+      mrg_jump_host(e->mrg, n_lo, n_hi);
+    }
+  }
 }
 
 bool is_pair_dist(int32_t kind) { return kind == GRNG_GAUSSIAN || kind == GRNG_LOGNORMAL; }

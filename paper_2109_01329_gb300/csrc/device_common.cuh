@@ -36,9 +36,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-// 128-bit counter from (lo, hi) 64-bit halves.
+// Philox counter of a block index given as (lo, hi) 64-bit halves.  Word
+// offsets live in Z / 2^128, so block indices live in Z / 2^126: the top two
+// bits are cleared, which makes word 2^128 + g equal to word g.
 __device__ __forceinline__ uint4 ctr_from(uint64_t lo, uint64_t hi) {
-  return make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+  return make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi,
+                    (uint32_t)(hi >> 32) & 0x3FFFFFFFu);
 }
 
 // (lo, hi) += v with carry.
