@@ -1,0 +1,478 @@
+"""Benchmark: the single-stream fill sweep at n = 10^9.
+
+One step = one pass of the whole path over the sweep workload: for each engine
+(Philox4x32-10, MRG32k3a) and each distribution (bits U32, uniform F32 and F64
+on [0, 1), Box-Muller gaussian F32 and F64, lognormal F32), create an engine
+(seed 2021, offset = this rank's shard), generate n outputs into a resident
+device buffer (the output of every fill, 4 or 8 GB, is far larger than L2) and
+advance the engine.  value = samples of all ranks / step time (Gsamples/s).
+
+Beside it: per-kernel achieved HBM write GB/s against the measured copy peak,
+the roofline of the dominant kernel, cuRAND's host API on the same fills
+(the native baseline of the paper, Sec. 3.2), an end-to-end number through
+the C ABI with host buffers (generate + device-to-host copy), clocks sampled
+during the timed region, and the CPU oracle as the timed CPU baseline.
+
+--impl reference times the oracle (plain CPU C++) on the host cores instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2109_01329_gb300 import workloads as W  # noqa: E402
+
+METRIC = "Gsamples/s and HBM-write GB/s (fraction of roofline) vs cuRAND; batched p50/p99"
+UNIT = "Gsamples/s"
+ENGINES = [(0, "philox4x32_10"), (1, "mrg32k3a")]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:  # noqa: BLE001
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- cuRAND
+class Curand:
+    """cuRAND host API through ctypes: the native baseline (timing only)."""
+
+    RNG = {0: 161, 1: 121}  # CURAND_RNG_PSEUDO_PHILOX4_32_10, CURAND_RNG_PSEUDO_MRG32K3A
+
+    def __init__(self):
+        lib = None
+        for name in ("libcurand.so", "libcurand.so.10"):
+            for d in ("", "/usr/local/cuda/lib64/", "/usr/local/cuda/targets/sbsa-linux/lib/"):
+                try:
+                    lib = ctypes.CDLL(d + name)
+                    break
+                except OSError:
+                    continue
+            if lib:
+                break
+        if lib is None:
+            raise RuntimeError("libcurand not found")
+        self.lib = lib
+        vp = ctypes.c_void_p
+        lib.curandCreateGenerator.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+        lib.curandSetPseudoRandomGeneratorSeed.argtypes = [vp, ctypes.c_ulonglong]
+        lib.curandSetStream.argtypes = [vp, vp]
+        lib.curandDestroyGenerator.argtypes = [vp]
+        lib.curandGenerate.argtypes = [vp, vp, ctypes.c_size_t]
+        lib.curandGenerateUniform.argtypes = [vp, vp, ctypes.c_size_t]
+        lib.curandGenerateUniformDouble.argtypes = [vp, vp, ctypes.c_size_t]
+        lib.curandGenerateNormal.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_float,
+                                             ctypes.c_float]
+        lib.curandGenerateNormalDouble.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_double,
+                                                   ctypes.c_double]
+        lib.curandGenerateLogNormal.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_float,
+                                                ctypes.c_float]
+
+    def generator(self, engine: int, seed: int, stream_ptr: int):
+        g = ctypes.c_void_p()
+        st = self.lib.curandCreateGenerator(ctypes.byref(g), self.RNG[engine])
+        if st != 0:
+            raise RuntimeError(f"curandCreateGenerator: {st}")
+        self.lib.curandSetPseudoRandomGeneratorSeed(g, seed)
+        self.lib.curandSetStream(g, ctypes.c_void_p(stream_ptr))
+        return g
+
+    def fill(self, g, name: str, ptr: int, n: int):
+        L, p = self.lib, ctypes.c_void_p(ptr)
+        if name == "bits_u32":
+            st = L.curandGenerate(g, p, n)
+        elif name == "uniform_f32":
+            st = L.curandGenerateUniform(g, p, n)
+        elif name == "uniform_f64":
+            st = L.curandGenerateUniformDouble(g, p, n)
+        elif name == "gaussian_f32":
+            st = L.curandGenerateNormal(g, p, n, 0.0, 1.0)
+        elif name == "gaussian_f64":
+            st = L.curandGenerateNormalDouble(g, p, n, 0.0, 1.0)
+        else:
+            st = L.curandGenerateLogNormal(g, p, n, 0.0, 1.0)
+        if st != 0:
+            raise RuntimeError(f"cuRAND {name}: status {st}")
+
+    def destroy(self, g):
+        self.lib.curandDestroyGenerator(g)
+
+
+# ----------------------------------------------------------------- oracle
+def oracle_rate(seconds_per_case: float, cores: int, n_cap: int):
+    """Oracle throughput on the host cores for each sweep case (bounded sample)."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    oracle.build()
+    rates, detail = {}, {}
+    chunk = 1 << 14
+    for ek, en in ENGINES:
+        for name, kind, dtype, p0, p1 in W.SWEEP_DISTS:
+            t0 = time.perf_counter()
+            done = 0
+            futs = []
+            with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+                idx = 0
+                while time.perf_counter() - t0 < seconds_per_case and done < n_cap:
+                    futs = [ex.submit(oracle.generate, ek, W.SWEEP_SEED,
+                                      oracle.words_for(kind, dtype, (idx + i) * chunk), kind,
+                                      dtype, p0, p1, chunk) for i in range(cores)]
+                    for f in futs:
+                        f.result()
+                    idx += cores
+                    done += cores * chunk
+            dt = time.perf_counter() - t0
+            rates[f"{en}/{name}"] = done / dt
+            detail[f"{en}/{name}"] = {"samples": done, "seconds": round(dt, 3)}
+    return rates, detail
+
+
+def aggregate_rate(rates: dict, n: int) -> float:
+    """Samples/s for the whole sweep step (n samples per case) at per-case rates."""
+    total_t = sum(n / r for r in rates.values())
+    return len(rates) * n / total_t
+
+
+def run_reference(args):
+    """The oracle as the reference arm: bounded samples of the sweep per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import concurrent.futures as cf
+
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    per_case = args.ref_samples
+    chunk = max(1, per_case // cores)
+
+    def step():
+        for ek, _ in ENGINES:
+            for name, kind, dtype, p0, p1 in W.SWEEP_DISTS:
+                with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+                    list(ex.map(lambda i: oracle.generate(
+                        ek, W.SWEEP_SEED, oracle.words_for(kind, dtype, i * chunk), kind, dtype,
+                        p0, p1, chunk), range(cores)))
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    samples = args.steps * len(ENGINES) * len(W.SWEEP_DISTS) * chunk * cores
+    value = samples / dt / 1e9
+    sample_desc = (f"{chunk * cores} samples per (engine, distribution) case per step, "
+                   f"{len(ENGINES) * len(W.SWEEP_DISTS)} cases, seed 2021, split over {cores} "
+                   "threads by word offset")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32/f32/f64", "data": "synthetic",
+            "config": {"workload": "fill sweep (bounded CPU sample): Philox4x32-10 and "
+                                   "MRG32k3a x {bits u32, uniform f32/f64, gaussian f32/f64, "
+                                   "lognormal f32}, seed 2021", "samples_per_case": chunk * cores},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample_desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+
+    import paper_2109_01329_gb300 as grng
+    from paper_2109_01329_gb300 import build as gbuild
+    from paper_2109_01329_gb300 import shard
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus != world and world > 1:
+        print(f"warning: --gpus {args.gpus} but WORLD_SIZE {world}", file=sys.stderr)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        gbuild.build()
+    if world > 1:
+        dist.barrier()
+    grng.load()
+
+    n = int(args.n)
+    hbm_peak, peak_src = _peaks()
+    stream = torch.cuda.current_stream(dev)
+    buf = torch.empty(n * 8, dtype=torch.uint8, device=dev)
+    tdt = {0: torch.int32, 1: torch.float32, 2: torch.float64}
+    cases = [(ek, en, d) for ek, en in ENGINES for d in W.SWEEP_DISTS]
+    if args.only:
+        cases = [c for c in cases if f"{c[1]}/{c[2][0]}" in args.only.split(",")]
+        if not cases:
+            raise SystemExit(f"--only {args.only}: no such case")
+    # weak scaling: rank r fills the r-th block of n outputs of one long stream
+    def rank_offset(kind, dtype):
+        return grng.words_for(grng.Distribution(kind, dtype, 0.0, 1.0), n) * rank
+
+    def one_step(events=None):
+        for i, (ek, en, (name, kind, dtype, p0, p1)) in enumerate(cases):
+            es = 8 if dtype == 2 else 4
+            out = buf[: n * es].view(tdt[dtype])
+            e = grng.Engine(ek, W.SWEEP_SEED, rank_offset(kind, dtype))
+            if events is not None:
+                events[i][0].record(stream)
+            grng.generate(grng.Distribution(kind, dtype, p0, p1), e, out)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(max(args.warmup, 0)):
+        one_step()
+    torch.cuda.synchronize()
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in cases] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        one_step(ev[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    samples_per_step = n * len(cases) * world
+    value = samples_per_step / (ms_per_step * 1e-3) / 1e9
+
+    per_kernel = {}
+    for i, (ek, en, (name, kind, dtype, p0, p1)) in enumerate(cases):
+        ms = statistics.median(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
+        es = 8 if dtype == 2 else 4
+        gbs = n * es / (ms * 1e-3) / 1e9
+        per_kernel[f"{en}/{name}"] = {"ms": round(ms, 4), "gsamples_s": round(n / ms / 1e6, 2),
+                                      "write_gbs": round(gbs, 1),
+                                      "frac_hbm": round(gbs / hbm_peak, 4)}
+    dom_name = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    dom = per_kernel[dom_name]
+    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": dom["write_gbs"],
+                "peak": hbm_peak, "unit": "GB/s", "frac": dom["frac_hbm"],
+                "traffic": args.traffic, "peak_source": f"{peak_src} hbm_gbs (copy)",
+                "bytes_per_launch": n * (8 if "f64" in dom_name else 4)}
+    target = per_kernel.get("philox4x32_10/uniform_f32", dom)
+
+    # cuRAND on the same fills (generate calls only; generator created outside)
+    curand = None
+    if not args.skip_curand and rank == 0:
+        try:
+            cr = Curand()
+            curand = {}
+            for ek, en, (name, kind, dtype, p0, p1) in cases:
+                es = 8 if dtype == 2 else 4
+                gen = cr.generator(ek, W.SWEEP_SEED, stream.cuda_stream)
+                for _ in range(2):
+                    cr.fill(gen, name, buf.data_ptr(), n)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 3
+                e0.record(stream)
+                for _ in range(reps):
+                    cr.fill(gen, name, buf.data_ptr(), n)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                cr.destroy(gen)
+                ours = per_kernel[f"{en}/{name}"]["ms"]
+                curand[f"{en}/{name}"] = {"ms": round(ms, 4), "gsamples_s": round(n / ms / 1e6, 2),
+                                          "speedup_ours": round(ms / ours, 3)}
+            tot_c = sum(v["ms"] for v in curand.values())
+            curand["_step_ms"] = round(tot_c, 3)
+            curand["_step_speedup_ours"] = round(tot_c / sum(v["ms"] for v in per_kernel.values()),
+                                                 3)
+        except Exception as ex:  # noqa: BLE001
+            curand = {"unavailable": str(ex)[:200]}
+
+    # end to end through the C ABI with host buffers (generate + D2H per chunk)
+    e2e = None
+    if not args.skip_e2e:
+        host = torch.empty(n * 8, dtype=torch.uint8, pin_memory=True)
+        work = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+        def e2e_step():
+            for ek, en, (name, kind, dtype, p0, p1) in cases:
+                es = 8 if dtype == 2 else 4
+                e = grng.Engine(ek, W.SWEEP_SEED, rank_offset(kind, dtype))
+                grng.generate_host(grng.Distribution(kind, dtype, p0, p1), e,
+                                   host[: n * es].view(tdt[dtype]), work)
+
+        e2e_step()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        d2h = sum(n * (8 if d[2] == 2 else 4) for _, _, d in cases)
+        e2e = {"value": samples_per_step * args.e2e_steps / dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
+               "ms_per_step": dt / args.e2e_steps * 1e3,
+               "how": "grng_generate_host into pinned host memory, 256 MiB device staging, "
+                      "host wall clock"}
+        del host, work
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        cores = os.cpu_count() or 1
+        rates, detail = oracle_rate(args.cpu_seconds, cores, n_cap=n)
+        cpu = {"value": aggregate_rate(rates, n) / 1e9, "unit": UNIT, "cores": cores,
+               "kind": "oracle",
+               "sample": f"about {args.cpu_seconds:g} s per (engine, distribution) case, "
+                         f"chunks of 16384 samples over {cores} threads by word offset; rate "
+                         "scaled to the sweep step (n per case)",
+               "per_case": {k: {"gsamples_s": round(rates[k] / 1e9, 6), **detail[k]}
+                            for k in rates}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32/f64",
+            "data": "synthetic",
+            "config": {"workload": f"fill sweep n={n:.0e} per GPU: Philox4x32-10 and MRG32k3a x "
+                                   "{bits u32, uniform f32 [0,1), uniform f64 [0,1), gaussian "
+                                   "f32 (0,1), gaussian f64 (0,1), lognormal f32 (0,1)}, "
+                                   "seed 2021",
+                       "n_per_fill": n, "fills_per_step": len(cases),
+                       "parallelism": f"shard{world} (rank r fills words from r * "
+                                      "words_for(n))",
+                       "l2": "every fill writes 4-8 GB, larger than the 129 MB L2"},
+            "roofline": roofline,
+            "target_philox_uniform_f32": {"write_gbs": target["write_gbs"],
+                                          "frac": target["frac_hbm"],
+                                          "gsamples_s": target["gsamples_s"]},
+            "per_kernel": per_kernel, "curand": curand, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clk, "gpu_launches": args.steps * len(cases)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=float, default=1e9)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=1.5)
+    ap.add_argument("--ref-samples", type=int, default=1 << 21)
+    ap.add_argument("--only", default="",
+                    help="comma-separated engine/distribution cases (profiling runs)")
+    ap.add_argument("--skip-curand", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per launch of the dominant kernel from an ncu capture")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
