@@ -197,6 +197,44 @@ GRNG_API grng_status grng_generate_host(const grng_distribution* dist, grng_engi
                                void* host_ptr, void* dev_work, size_t work_bytes,
                                grng_stream_t stream);
 
+/*
+ * Size of the library's static device staging array used by
+ * grng_generate_host_static (64 MiB, held on every GPU that loads the
+ * library until the process exits).
+ */
+#define GRNG_STATIC_STAGE_BYTES (64u << 20)
+
+/*
+ * The paper has no counterpart to this function.  It is grng_generate_host
+ * for callers that cannot allocate device memory at the point of the call:
+ * an application whose own memory pool already owns the whole device, code
+ * that must not call cudaMalloc / cudaFree because they can synchronise the
+ * device, or a plug-in whose host forbids device allocations after start-up.
+ * Instead of a caller-provided device buffer it stages through a fixed
+ * array inside the library (GRNG_STATIC_STAGE_BYTES per device), and it
+ * allocates nothing, on the device or the host.
+ *
+ * Fills host_ptr[0 .. n) like grng_generate(dist, engine, n, ...) followed by
+ * a device-to-host copy on `stream`, and returns after the copy completed
+ * (synchronises `stream`).  The values and the engine's advance equal those
+ * of grng_generate.  host_ptr may be pinned or pageable.
+ *   n * element size must not exceed GRNG_STATIC_STAGE_BYTES: larger
+ *   requests return GRNG_ERR_UNSUPPORTED (split them into several calls; the
+ *   engine continues its sequence across calls).
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture begins.
+ *   All calls share the one array.  The library serialises its own calls
+ *   and waits for each copy, so calls from one process do not overlap on the
+ *   GPU; calls that did overlap would race on the array.  Nothing in it has
+ *   to start at zero: every element copied out is written first.
+ * Errors: as grng_generate; UNSUPPORTED above the size limit; CUDA if the
+ * copy fails (the engine is then moved back to where it was).
+ */
+GRNG_API grng_status grng_generate_host_static(const grng_distribution* dist,
+                                               grng_engine_t engine, int64_t n,
+                                               void* host_ptr, grng_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ U32, F32, F64 = 0, 1, 2
 EXPORTED = ["grng_status_string", "grng_last_error", "grng_engine_create", "grng_engine_restore",
             "grng_engine_copy", "grng_engine_skip_ahead", "grng_engine_get_state",
             "grng_engine_destroy", "grng_words_for", "grng_generate",
-            "grng_generate_substreams", "grng_generate_host"]
+            "grng_generate_substreams", "grng_generate_host", "grng_generate_host_static"]
 
 
 class GrngError(RuntimeError):
@@ -82,6 +82,8 @@ def load() -> ctypes.CDLL:
                                                vp, vp]
         L.grng_generate_host.argtypes = [ctypes.POINTER(_Dist), vp, ctypes.c_int64, vp, vp,
                                          ctypes.c_size_t, vp]
+        L.grng_generate_host_static.argtypes = [ctypes.POINTER(_Dist), vp, ctypes.c_int64, vp,
+                                                vp]
         for name in EXPORTED[2:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -291,4 +293,28 @@ def generate_host(dist: Distribution, engine: Engine, host_out, work, stream=Non
                                          ctypes.c_void_p(work.data_ptr()), nbytes,
                                          ctypes.c_void_p(_stream_ptr(work.device, stream))),
                "grng_generate_host")
+    return host_out
+
+
+STATIC_STAGE_BYTES = 64 << 20  # GRNG_STATIC_STAGE_BYTES
+
+
+def generate_host_static(dist: Distribution, engine: Engine, host_out, n: int | None = None,
+                         stream=None, device=None):
+    """grng_generate_host_static: fills a CPU tensor through the library's own
+    static device staging array (no allocation; n * element size must not
+    exceed STATIC_STAGE_BYTES).  Synchronous."""
+    import torch
+
+    if host_out.is_cuda or not host_out.is_contiguous() or not _torch_dtype_ok(host_out,
+                                                                                 dist.dtype):
+        raise ValueError("host_out must be a contiguous CPU tensor of the distribution's dtype")
+    n = host_out.numel() if n is None else n
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    d = dist._c()
+    with torch.cuda.device(dev):
+        _check(load().grng_generate_host_static(ctypes.byref(d), engine.handle, n,
+                                                ctypes.c_void_p(host_out.data_ptr()),
+                                                ctypes.c_void_p(_stream_ptr(dev, stream))),
+               "grng_generate_host_static")
     return host_out

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libgrng.so")
 
-SOURCES = ["capi.cpp", "philox_kernels.cu", "mrg_kernels.cu"]
+SOURCES = ["capi.cpp", "philox_kernels.cu", "mrg_kernels.cu", "static_stage.cu"]
 HEADERS = ["device_common.cuh", "grng_internal.h", "mrg_tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
