@@ -8,10 +8,10 @@
 //
 // Output is cut into 16-byte groups at 16-byte aligned addresses.  Every
 // variant consumes exactly 4 words per 16 output bytes, so:
-//   * fast kernel: when the word phase of the first group matches its block
-//     boundary (and Box-Muller pairs do not straddle groups), group j is
-//     exactly Philox block base + j: one block, one transform, one st.v4.
-//     Only the first and the last group may be partial.
+//   * stream / multi kernels: when the word phase of the first group matches
+//     its block boundary (and Box-Muller pairs do not straddle groups), group
+//     j is exactly Philox block base + j: one block, one transform, one
+//     st.v4.  Only the first and the last group of a stream may be partial.
 //   * staged kernel: any other phase.  A CTA computes the blocks covering a
 //     tile of 256 groups into shared memory, then each thread assembles its
 //     group from the words it needs.
@@ -31,31 +31,13 @@ using namespace dev;
 
 constexpr int kThreads = 256;
 
-struct FastParams {
-  TransformParams t;
-  void* out;
-  int64_t n;          // elements per stream
-  int64_t groups;     // 16-byte groups per stream
-  int64_t total;      // groups * num_streams
-  int64_t head;       // elements of group 0 that lie before `out`
-  uint64_t base_lo;   // block counter of group 0 of stream 0
-  uint64_t base_hi;
-  uint64_t sb_lo;     // block-counter stride between streams
-  uint64_t sb_hi;
-  int64_t tq;         // grid stride = tq * groups + tr (multi-stream walk)
-  int64_t tr;
-  uint64_t tqsb_lo;   // tq * sb
-  uint64_t tqsb_hi;
-  uint32_t k0, k1;
-};
-
 __device__ __forceinline__ void add128(uint64_t& lo, uint64_t& hi, uint64_t vlo, uint64_t vhi) {
   const uint64_t s = lo + vlo;
   hi += vhi + ((s < lo) ? 1u : 0u);
   lo = s;
 }
 
-// Stores the in-range elements of a partial group.
+// Stores the in-range elements of a partial group whose first element is e0.
 template <int V>
 __device__ __forceinline__ void store_partial(char* stream_base, int64_t e0, int64_t n, uint4 o) {
   using I = VInfo<V>;
@@ -74,47 +56,93 @@ __device__ __forceinline__ void store_partial(char* stream_base, int64_t e0, int
   }
 }
 
-template <int V, bool kMulti>
-__global__ void __launch_bounds__(kThreads) philox_fast_kernel(const FastParams p) {
+// ------------------------------------------------------------ single stream
+// Full 16-byte groups [jf, jl) in the main loop, U independent counter blocks
+// per thread per iteration (stores of the U blocks are each coalesced across
+// the warp), pointer and counter advanced by increments.  The at most two
+// partial groups (the first and the last) are done by the grid's first two
+// threads before the loop.
+struct StreamParams {
+  TransformParams t;
+  uint4* gbase;       // 16-byte aligned address of group 0 (may precede out)
+  void* out;
+  int64_t n;          // elements
+  int64_t head;       // elements of group 0 that lie before out
+  int64_t jf, jl;     // full groups [jf, jl)
+  int64_t edge[2];    // partial groups, or -1
+  uint64_t base_lo;   // block counter of group 0
+  uint64_t base_hi;
+  uint32_t k0, k1;
+};
+
+template <int V, bool kHiUniform>
+__device__ __forceinline__ uint4 group_block(const StreamParams& p, uint64_t j) {
+  const uint64_t lo = p.base_lo + j;
+  const uint64_t hi = kHiUniform ? p.base_hi : p.base_hi + ((lo < p.base_lo) ? 1u : 0u);
+  return philox4x32_10(ctr_from(lo, hi), p.k0, p.k1);
+}
+
+template <int V, int U, bool kHiUniform>
+__global__ void __launch_bounds__(kThreads) philox_stream_kernel(const StreamParams p) {
   using I = VInfo<V>;
   constexpr int kEpg = 16 / I::es;
-  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  const int64_t T = (int64_t)gridDim.x * kThreads;
+  const int64_t tid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (tid < 2 && p.edge[tid] >= 0) {
+    const int64_t j = p.edge[tid];
+    const uint4 o = block_outputs<V>(group_block<V, false>(p, (uint64_t)j), p.t);
+    store_partial<V>(reinterpret_cast<char*>(p.out), j * kEpg - p.head, p.n, o);
+  }
+  int64_t j = p.jf + tid;
+  uint4* dst = p.gbase + j;
+  for (; j + (U - 1) * T < p.jl; j += U * T, dst += U * T) {
+    uint4 o[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      o[u] = block_outputs<V>(group_block<V, kHiUniform>(p, (uint64_t)(j + u * T)), p.t);
+#pragma unroll
+    for (int u = 0; u < U; ++u) dst[u * T] = o[u];
+  }
+  for (; j < p.jl; j += T, dst += T)
+    *dst = block_outputs<V>(group_block<V, kHiUniform>(p, (uint64_t)j), p.t);
+}
+
+// ------------------------------------------------------------ substreams
+// num_streams streams whose every group is full (16-byte aligned streams of
+// whole groups); stream s, group j is block base + s * sb + j.
+struct MultiParams {
+  TransformParams t;
+  uint4* out;
+  int64_t groups;     // groups per stream
+  int64_t total;      // groups * num_streams
+  uint64_t base_lo, base_hi;
+  uint64_t sb_lo, sb_hi;      // block-counter stride between streams
+  int64_t tq, tr;             // grid stride = tq * groups + tr
+  uint64_t tqsb_lo, tqsb_hi;  // tq * sb
+  uint32_t k0, k1;
+};
+
+template <int V>
+__global__ void __launch_bounds__(kThreads) philox_multi_kernel(const MultiParams p) {
+  const int64_t T = (int64_t)gridDim.x * kThreads;
   int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (idx >= p.total) return;
-
-  int64_t s = 0;
-  int64_t j = idx;
+  int64_t s = idx / p.groups;
+  int64_t j = idx - s * p.groups;
   uint64_t sb_lo = p.base_lo, sb_hi = p.base_hi;  // block counter of group 0 of stream s
-  if constexpr (kMulti) {
-    s = idx / p.groups;
-    j = idx - s * p.groups;
-    // sb += s * (sb_lo, sb_hi)
+  {
     const uint64_t us = (uint64_t)s;
     add128(sb_lo, sb_hi, us * p.sb_lo, __umul64hi(us, p.sb_lo) + us * p.sb_hi);
   }
-  for (; idx < p.total; idx += stride) {
+  for (; idx < p.total; idx += T) {
     uint64_t c_lo = sb_lo, c_hi = sb_hi;
     add128(c_lo, c_hi, (uint64_t)j, 0);
-    const uint4 blk = philox4x32_10(ctr_from(c_lo, c_hi), p.k0, p.k1);
-    const uint4 o = block_outputs<V>(blk, p.t);
-    char* sbase = reinterpret_cast<char*>(p.out) + (s * p.n) * I::es;
-    const int64_t e0 = j * kEpg - p.head;
-    if (e0 >= 0 && e0 + kEpg <= p.n) {
-      store16(sbase + e0 * I::es, o);
-    } else {
-      store_partial<V>(sbase, e0, p.n, o);
-    }
-    if constexpr (kMulti) {
-      j += p.tr;
-      s += p.tq;
-      add128(sb_lo, sb_hi, p.tqsb_lo, p.tqsb_hi);
-      if (j >= p.groups) {
-        j -= p.groups;
-        s += 1;
-        add128(sb_lo, sb_hi, p.sb_lo, p.sb_hi);
-      }
-    } else {
-      j += stride;
+    p.out[idx] = block_outputs<V>(philox4x32_10(ctr_from(c_lo, c_hi), p.k0, p.k1), p.t);
+    j += p.tr;
+    add128(sb_lo, sb_hi, p.tqsb_lo, p.tqsb_hi);
+    if (j >= p.groups) {
+      j -= p.groups;
+      add128(sb_lo, sb_hi, p.sb_lo, p.sb_hi);
     }
   }
 }
@@ -238,41 +266,77 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
   const bool fast = uniform_streams && ((r.off_lo - phase_w) & 3u) == 0 &&
                     (phase_w % (uint32_t)I::wpu) == 0;
 
-  if (fast) {
-    FastParams p;
+  // base block counter = (off - phase_w) / 4 with a 128-bit borrow
+  const uint64_t lo0 = r.off_lo - phase_w;
+  const uint64_t hi0 = r.off_hi - ((r.off_lo < phase_w) ? 1u : 0u);
+  const uint64_t base_lo = (lo0 >> 2) | (hi0 << 62);
+  const uint64_t base_hi = hi0 >> 2;
+  const int64_t head = (int64_t)(phase_w * 4u / I::es);
+  const int64_t groups = (head + r.n + kEpg - 1) / kEpg;
+  if (fast && r.num_streams == 1) {
+    StreamParams p;
     p.t = r.t;
     p.out = r.out;
+    p.gbase = reinterpret_cast<uint4*>(addr - phase_w * 4u);
     p.n = r.n;
-    p.head = (int64_t)(phase_w * 4u / I::es);
-    p.groups = (p.head + r.n + kEpg - 1) / kEpg;
-    p.total = p.groups * r.num_streams;
-    // base block counter = (off - phase_w) / 4 with a 128-bit borrow
-    uint64_t lo = r.off_lo - phase_w;
-    uint64_t hi = r.off_hi - ((r.off_lo < phase_w) ? 1u : 0u);
-    p.base_lo = (lo >> 2) | (hi << 62);
-    p.base_hi = hi >> 2;
+    p.head = head;
+    p.base_lo = base_lo;
+    p.base_hi = base_hi;
+    p.k0 = r.key[0];
+    p.k1 = r.key[1];
+    // full groups: the first group is partial when head > 0, the last one
+    // when the end is not on a group boundary (or both are the same group)
+    int64_t jf = head > 0 ? 1 : 0;
+    int64_t jl = ((head + r.n) % kEpg) != 0 ? groups - 1 : groups;
+    p.edge[0] = p.edge[1] = -1;
+    if (jf > jl) {  // a single partial group
+      p.edge[0] = 0;
+      jf = jl = 0;
+    } else {
+      if (head > 0) p.edge[0] = 0;
+      if (jl < groups) p.edge[1] = groups - 1;
+    }
+    p.jf = jf;
+    p.jl = jl;
+    constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 4 : 2;
+    const bool hi_uniform = base_lo + (uint64_t)groups >= base_lo;  // no carry into the top half
+    auto kernel = hi_uniform ? philox_stream_kernel<V, kU, true>
+                             : philox_stream_kernel<V, kU, false>;
+    static int occ[2] = {0, 0};
+    int& o = occ[hi_uniform ? 1 : 0];
+    if (o == 0) o = blocks_per_sm(kernel);
+    const int64_t work = (jl - jf + (int64_t)kU - 1) / kU;
+    int64_t grid = (work + kThreads - 1) / kThreads;
+    if (grid < 1) grid = 1;
+    const int64_t cap = (int64_t)sms * o;
+    if (grid > cap) grid = cap;
+    kernel<<<(unsigned)grid, kThreads, 0, stream>>>(p);
+  } else if (fast && head == 0 && (stream_bytes % 16u) == 0) {
+    MultiParams p;
+    p.t = r.t;
+    p.out = reinterpret_cast<uint4*>(r.out);
+    p.groups = groups;
+    p.total = groups * r.num_streams;
+    p.base_lo = base_lo;
+    p.base_hi = base_hi;
     p.sb_lo = (r.stride_lo >> 2) | (r.stride_hi << 62);
     p.sb_hi = r.stride_hi >> 2;
     p.k0 = r.key[0];
     p.k1 = r.key[1];
-    const bool multi = r.num_streams > 1;
-    auto kernel = multi ? philox_fast_kernel<V, true> : philox_fast_kernel<V, false>;
-    static int occ[2] = {0, 0};
-    int& o = occ[multi ? 1 : 0];
-    if (o == 0) o = blocks_per_sm(kernel);
+    static int occ = 0;
+    if (occ == 0) occ = blocks_per_sm(philox_multi_kernel<V>);
     int64_t grid = (p.total + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)sms * o;
+    const int64_t cap = (int64_t)sms * occ;
     if (grid > cap) grid = cap;
     const int64_t gstride = grid * kThreads;
     p.tq = gstride / p.groups;
     p.tr = gstride - p.tq * p.groups;
-    // tq * sb (tq < 2^31)
     const unsigned __int128 tqsb =
         (unsigned __int128)(uint64_t)p.tq *
         (((unsigned __int128)p.sb_hi << 64) | (unsigned __int128)p.sb_lo);
     p.tqsb_lo = (uint64_t)tqsb;
     p.tqsb_hi = (uint64_t)(tqsb >> 64);
-    kernel<<<(unsigned)grid, kThreads, 0, stream>>>(p);
+    philox_multi_kernel<V><<<(unsigned)grid, kThreads, 0, stream>>>(p);
   } else {
     StagedParams p;
     p.t = r.t;
