@@ -183,6 +183,18 @@ GRNG_API grng_status grng_generate_substreams(const grng_distribution* dist, grn
                                      grng_stream_t stream);
 
 /*
+ * Applies `dist` to caller-supplied words: dev_out[0 .. n) receives the n
+ * outputs that grng_generate would produce from the word sequence
+ * dev_words[0 .. grng_words_for(dist, n)) (the transform of Sec. 3.3,
+ * Listing 2 and of the distribution objects of Sec. 3.1, without an engine).
+ * For bit sources other than the two engines, and for checking the
+ * transforms on chosen inputs.  dev_words: device memory, 4-byte aligned,
+ * owned by the caller.  Same errors as grng_generate (no engine involved).
+ */
+GRNG_API grng_status grng_transform_words(const grng_distribution* dist, const uint32_t* dev_words,
+                                          int64_t n, void* dev_out, grng_stream_t stream);
+
+/*
  * The RNG-burner flow of Sec. 4.1 / Sec. 6 (generate, then copy the output
  * to the host): fills host_ptr[0 .. n) like grng_generate, staging through
  * the caller's device buffer dev_work of work_bytes bytes (at least 2 MiB,

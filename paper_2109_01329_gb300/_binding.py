@@ -27,7 +27,8 @@ U32, F32, F64 = 0, 1, 2
 EXPORTED = ["grng_status_string", "grng_last_error", "grng_engine_create", "grng_engine_restore",
             "grng_engine_copy", "grng_engine_skip_ahead", "grng_engine_get_state",
             "grng_engine_destroy", "grng_words_for", "grng_generate",
-            "grng_generate_substreams", "grng_generate_host", "grng_generate_host_static"]
+            "grng_generate_substreams", "grng_generate_host", "grng_generate_host_static",
+            "grng_transform_words"]
 
 
 class GrngError(RuntimeError):
@@ -84,6 +85,7 @@ def load() -> ctypes.CDLL:
                                          ctypes.c_size_t, vp]
         L.grng_generate_host_static.argtypes = [ctypes.POINTER(_Dist), vp, ctypes.c_int64, vp,
                                                 vp]
+        L.grng_transform_words.argtypes = [ctypes.POINTER(_Dist), vp, ctypes.c_int64, vp, vp]
         for name in EXPORTED[2:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -318,3 +320,23 @@ def generate_host_static(dist: Distribution, engine: Engine, host_out, n: int | 
                                                 ctypes.c_void_p(_stream_ptr(dev, stream))),
                "grng_generate_host_static")
     return host_out
+
+
+def transform_words(dist: Distribution, words, out, n: int | None = None, stream=None):
+    """grng_transform_words: applies dist to the device words tensor (int32 / uint32)."""
+    import torch
+
+    if not (words.is_cuda and out.is_cuda and words.is_contiguous() and out.is_contiguous()):
+        raise ValueError("words and out must be contiguous CUDA tensors")
+    if not _torch_dtype_ok(out, dist.dtype):
+        raise ValueError("out dtype does not match the distribution")
+    n = out.numel() if n is None else n
+    if words.numel() * words.element_size() < 4 * words_for(dist, n):
+        raise ValueError("not enough words")
+    d = dist._c()
+    with torch.cuda.device(out.device):
+        _check(load().grng_transform_words(ctypes.byref(d), ctypes.c_void_p(words.data_ptr()), n,
+                                           ctypes.c_void_p(out.data_ptr()),
+                                           ctypes.c_void_p(_stream_ptr(out.device, stream))),
+               "grng_transform_words")
+    return out

@@ -20,8 +20,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libgrng.so")
 
-SOURCES = ["capi.cpp", "philox_kernels.cu", "mrg_kernels.cu", "static_stage.cu"]
-HEADERS = ["device_common.cuh", "grng_internal.h", "mrg_tables.h"]
+SOURCES = ["capi.cpp", "philox_kernels.cu", "mrg_kernels.cu", "static_stage.cu",
+           "transform_kernels.cu"]
+HEADERS = ["device_common.cuh", "grng_internal.h", "mrg_tables.h", "bm64_fixed.cuh",
+           "bm64_tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

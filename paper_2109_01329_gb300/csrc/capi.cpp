@@ -212,6 +212,7 @@ int choose_variant(const grng_distribution* d, TransformParams* t) {
       }
       t->dmean = d->p0;
       t->dsd = d->p1;
+      t->std_normal = (d->p0 == 0.0 && d->p1 == 1.0) ? 1 : 0;
       return logn ? V_LOGN_F64 : V_GAUSS_F64;
     }
     default: return -1;
@@ -432,6 +433,30 @@ grng_status grng_generate(const grng_distribution* dist, grng_engine_t engine, i
   if (st != GRNG_OK) return st;
   advance_engine(engine, words_for_checked(dist, n), 0);
   return GRNG_OK;
+}
+
+grng_status grng_transform_words(const grng_distribution* dist, const uint32_t* dev_words,
+                                 int64_t n, void* dev_out, grng_stream_t stream) {
+  grng_status st = check_dist(dist);
+  if (st != GRNG_OK) return st;
+  if (n < 0) {
+    set_error("n < 0");
+    return GRNG_ERR_INVALID_ARG;
+  }
+  if (n > kMaxElements) {
+    set_error("n above 2^40");
+    return GRNG_ERR_UNSUPPORTED;
+  }
+  st = check_ptr(dev_out, n, dist->dtype);
+  if (st != GRNG_OK) return st;
+  if (n > 0 && (dev_words == nullptr || ((uintptr_t)dev_words & 3u) != 0)) {
+    set_error("words pointer is NULL or not 4-byte aligned");
+    return GRNG_ERR_INVALID_ARG;
+  }
+  if (n == 0) return GRNG_OK;
+  TransformParams t;
+  const int v = choose_variant(dist, &t);
+  return launch_transform(v, t, dev_words, n, dev_out, (cudaStream_t)stream);
 }
 
 grng_status grng_generate_substreams(const grng_distribution* dist, grng_engine_t engine,

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 
+#include "bm64_fixed.cuh"
 #include "grng_internal.h"
 
 namespace grng {
@@ -112,15 +113,11 @@ __device__ __forceinline__ void box_muller_f32(uint32_t w0, uint32_t w1, float& 
   z1 = rho * s;
 }
 
+// FP64 pair: integer fixed-point evaluation (see bm64_fixed.cuh), within
+// about 1 ulp of the exact value, without the FP64 pipe.
 __device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
                                                double& z0, double& z1) {
-  const double u1 = scaled_u54_to_f64(u53(w0, w1) + 1u, -53);
-  const double two_u2 = scaled_u54_to_f64(u53(w2, w3), -52);
-  const double rho = sqrt(-2.0 * log(u1));
-  double s, c;
-  sincospi(two_u2, &s, &c);
-  z0 = rho * c;
-  z1 = rho * s;
+  bm64::box_muller(u53(w0, w1), u53(w2, w3), z0, z1);
 }
 
 // ------------------------------------------------- one unit -> its outputs
@@ -160,8 +157,11 @@ __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
   } else {  // V_GAUSS_F64, V_LOGN_F64
     double z0, z1;
     box_muller_f64(w[0], w[1], w[2], w[3], z0, z1);
-    double y0 = fma(t.dsd, z0, t.dmean);
-    double y1 = fma(t.dsd, z1, t.dmean);
+    double y0 = z0, y1 = z1;
+    if (!t.std_normal) {  // mean + sd z: fma(1, z, 0) == z, so (0, 1) skips it exactly
+      y0 = fma(t.dsd, z0, t.dmean);
+      y1 = fma(t.dsd, z1, t.dmean);
+    }
     if constexpr (V == V_LOGN_F64) {
       y0 = exp(y0);
       y1 = exp(y1);

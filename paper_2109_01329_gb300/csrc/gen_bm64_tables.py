@@ -1,0 +1,69 @@
+"""Writes bm64_tables.h: constants of the integer FP64 Box-Muller transform.
+
+Run from this directory: ``python gen_bm64_tables.py > bm64_tables.h``.
+Values are computed with mpmath at 200 bits and rounded to nearest.
+
+Tables (emitted as initializer macros GRNG_BM64_LOGC, _LOGT, _SINT, _COST)
+  kLogC[i], i = 0..512:  c_i = floor(2^24 / (1 - i/1024)) / 2^24, the reduction
+                         factor for -ln(1 - delta) with delta in [i/1024, (i+1)/1024)
+  kLogT[i]:              ln(c_i) * 2^64 (c_i exactly as stored)
+  kSinT[j], kCosT[j], j = 0..256:  sin, cos(2 pi j / 2048) * 2^63
+Scalars
+  kLn2:    ln 2 * 2^64
+  k2Pi61:  2 pi * 2^61
+  kInv2 .. kInv7: 2^64 / k (truncated)
+  kInv24_32, kInv120_32, kInv720_32: 2^64 / 6 and 2^32 / {24, 120, 720}
+"""
+
+import mpmath as mp
+
+mp.mp.prec = 200
+
+
+def rnd(x):
+    return int(mp.nint(x))
+
+
+def main():
+    out = []
+    out.append("// Generated by gen_bm64_tables.py (mpmath, 200-bit); do not edit.")
+    out.append("#pragma once")
+    out.append("#include <cstdint>")
+    out.append("namespace grng {")
+    out.append("namespace bm64 {")
+    two24 = mp.mpf(2) ** 24
+    two63 = mp.mpf(2) ** 63
+    two64 = mp.mpf(2) ** 64
+    logc, logt = [], []
+    for i in range(513):
+        c = int(mp.floor(two24 / (1 - mp.mpf(i) / 1024)))
+        logc.append(c)
+        logt.append(rnd(mp.log(mp.mpf(c) / two24) * two64))
+    assert logc[0] == 1 << 24 and logc[512] == 1 << 25
+    assert all(t < 1 << 64 for t in logt)
+    sint = [rnd(mp.sin(2 * mp.pi * j / 2048) * two63) for j in range(257)]
+    cost = [rnd(mp.cos(2 * mp.pi * j / 2048) * two63) for j in range(257)]
+
+    out.append(f"constexpr uint64_t kLn2 = {rnd(mp.log(2) * two64)}ull;")
+    out.append(f"constexpr uint64_t k2Pi61 = {rnd(2 * mp.pi * mp.mpf(2) ** 61)}ull;")
+    for k in range(2, 8):
+        out.append(f"constexpr uint64_t kInv{k} = {(1 << 64) // k}ull;")
+    out.append(f"constexpr uint32_t kInv24_32 = {rnd(mp.mpf(2) ** 32 / 24)}u;")
+    out.append(f"constexpr uint32_t kInv120_32 = {rnd(mp.mpf(2) ** 32 / 120)}u;")
+    out.append(f"constexpr uint32_t kInv720_32 = {rnd(mp.mpf(2) ** 32 / 720)}u;")
+    # table bodies as macros: the device and host copies are declared where used
+    for name, ctype, vals in [("LOGC", "uint32_t", logc), ("LOGT", "uint64_t", logt),
+                              ("SINT", "uint64_t", sint), ("COST", "uint64_t", cost)]:
+        suffix = "ull" if "64" in ctype else "u"
+        out.append(f"#define GRNG_BM64_{name}_LEN {len(vals)}")
+        out.append(f"#define GRNG_BM64_{name} {{ \\")
+        for k in range(0, len(vals), 4):
+            out.append("    " + ", ".join(f"{v}{suffix}" for v in vals[k:k + 4]) + ", \\")
+        out.append("}")
+    out.append("}  // namespace bm64")
+    out.append("}  // namespace grng")
+    print("\n".join(out))
+
+
+if __name__ == "__main__":
+    main()

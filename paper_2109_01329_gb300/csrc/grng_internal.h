@@ -51,7 +51,7 @@ struct TransformParams {
   double dmean, dsd;          // F64 gaussian / lognormal
   int64_t aff_a;              // F64 exact affine: r = (aff_a + x) 2^aff_exp, x = 53-bit word
   int32_t aff_exp;
-  int32_t pad;
+  int32_t std_normal;         // F64 gaussian / lognormal with (0, 1): skip mean + sd z
 };
 
 // One fill request as the launchers see it: num_streams streams of n
@@ -73,6 +73,9 @@ struct FillRequest {
 // Kernel launchers; return GRNG_OK or GRNG_ERR_CUDA (detail via set_error).
 grng_status launch_philox(const FillRequest& r, CUstream_st* stream);
 grng_status launch_mrg(const FillRequest& r, CUstream_st* stream);
+// Applies a variant to n outputs' worth of caller-supplied device words.
+grng_status launch_transform(int variant, const TransformParams& t, const uint32_t* words,
+                             int64_t n, void* out, CUstream_st* stream);
 
 // Records an error message for grng_last_error() on this thread.
 void set_error(const char* fmt, ...);

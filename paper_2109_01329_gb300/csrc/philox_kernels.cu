@@ -298,7 +298,9 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     }
     p.jf = jf;
     p.jl = jl;
-    constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 4 : 2;
+    constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 4
+                       : (V == V_GAUSS_F64 || V == V_LOGN_F64)          ? 1
+                                                                         : 2;
     const bool hi_uniform = base_lo + (uint64_t)groups >= base_lo;  // no carry into the top half
     auto kernel = hi_uniform ? philox_stream_kernel<V, kU, true>
                              : philox_stream_kernel<V, kU, false>;
