@@ -84,6 +84,24 @@ GRNG_BM_HD uint64_t umulhi(uint64_t a, uint64_t b) {
 #endif
 }
 
+// High 64 bits of a * b from three 32x32 -> 64-bit products: the low x low
+// product and the carry out of the low halves of the two cross products are
+// dropped, so the result is at most 2 below the exact high word (2 units of
+// the 2^-64 scale used throughout).  Where two halves of one product are
+// spliced together the exact form below is used instead.
+GRNG_BM_HD uint64_t umulhi_apx(uint64_t a, uint64_t b) {
+  const uint64_t ah = a >> 32, al = (uint32_t)a, bh = b >> 32, bl = (uint32_t)b;
+  return ah * bh + ((ah * bl) >> 32) + ((al * bh) >> 32);
+}
+
+// Exact 96-bit product of a 64-bit and a 32-bit value: hi = (a c) >> 32,
+// lo32 = (a c) mod 2^32.
+GRNG_BM_HD void mul64x32(uint64_t a, uint32_t c, uint64_t& hi, uint32_t& lo32) {
+  const uint64_t l = (a & 0xFFFFFFFFull) * c;
+  hi = (a >> 32) * c + (l >> 32);
+  lo32 = (uint32_t)l;
+}
+
 GRNG_BM_HD int clz64(uint64_t x) {  // x != 0
 #if defined(__CUDA_ARCH__)
   return __clzll((long long)x);
@@ -108,22 +126,27 @@ GRNG_BM_HD void neg_log(uint64_t m1, uint64_t& lm, int& le) {
   const uint64_t M = m1 << (63 - q);        // (1 - delta) 2^64, top bit set
   const uint64_t D = 0ull - M;              // delta 2^64 in (0, 2^63]
   const uint32_t i = (uint32_t)(D >> 54);   // 0..512
-  const uint64_t C = logc(i);               // c_i 2^24
-  // r 2^64 = 2^64 - M C 2^-24 (truncating M C 2^-24 leaves r >= 0)
-  const uint64_t phi = umulhi(M, C);
-  const uint64_t plo = M * C;
-  const uint64_t R = 0ull - ((phi << 40) | (plo >> 24));
+  const uint32_t C = logc(i);               // c_i 2^24
+  // r 2^64 = 2^64 - M C 2^-24 (truncating M C 2^-24 leaves r >= 0); the
+  // 96-bit product M C is exact, and M C 2^-24 = (hi << 8) | (lo32 >> 24)
+  uint64_t mc_hi;
+  uint32_t mc_lo;
+  mul64x32(M, C, mc_hi, mc_lo);
+  const uint64_t R = 0ull - ((mc_hi << 8) | (uint64_t)(mc_lo >> 24));
   // -ln(1 - r) = r + r^2 (1/2 + r/3 + r^2/4 + r^3/5 + r^4/6 + r^5/7)
   uint64_t B = kInv7;
-  B = kInv6 + umulhi(R, B);
-  B = kInv5 + umulhi(R, B);
-  B = kInv4 + umulhi(R, B);
-  B = kInv3 + umulhi(R, B);
-  B = kInv2 + umulhi(R, B);
-  const uint64_t S = R + umulhi(umulhi(R, R), B);
-  // L 2^64 = e ln 2 + ln c_i + S, as a 128-bit sum
-  uint64_t lo = kLn2 * e;
-  uint64_t hi = umulhi(kLn2, e);
+  B = kInv6 + umulhi_apx(R, B);
+  B = kInv5 + umulhi_apx(R, B);
+  B = kInv4 + umulhi_apx(R, B);
+  B = kInv3 + umulhi_apx(R, B);
+  B = kInv2 + umulhi_apx(R, B);
+  const uint64_t S = R + umulhi_apx(umulhi_apx(R, R), B);
+  // L 2^64 = e ln 2 + ln c_i + S, as a 128-bit sum (e ln 2 exactly: 64 x 32)
+  uint64_t ln2e_hi;
+  uint32_t ln2e_lo;
+  mul64x32(kLn2, (uint32_t)e, ln2e_hi, ln2e_lo);
+  uint64_t lo = (ln2e_hi << 32) | ln2e_lo;
+  uint64_t hi = ln2e_hi >> 32;
   const uint64_t T = logt(i);
   lo += T;
   hi += (lo < T) ? 1u : 0u;
@@ -157,13 +180,13 @@ GRNG_BM_HD void sqrt2x(uint64_t lm, int le, uint64_t& sq, int& se) {
   uint64_t Y = (uint64_t)((yb & 0x7FFFFFu) | 0x800000u) << (39 + ey);
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const uint64_t Y2 = umulhi(Y, Y);                 // y^2 2^60
-    const uint64_t XY2 = umulhi(X, Y2);               // x y^2 2^60
+    const uint64_t Y2 = umulhi_apx(Y, Y);             // y^2 2^60
+    const uint64_t XY2 = umulhi_apx(X, Y2);           // x y^2 2^60
     const uint64_t Tm = (3ull << 60) - XY2;           // (3 - x y^2) 2^60
-    Y = umulhi(Y, Tm) << 3;                           // y (3 - x y^2) / 2 2^62
+    Y = umulhi_apx(Y, Tm) << 3;                       // y (3 - x y^2) / 2 2^62
   }
   // sqrt(x) 2^62 (kept below 2^62 + error: no shift, so no wrap near x = 1)
-  sq = umulhi(X, Y);
+  sq = umulhi_apx(X, Y);
   // sqrt(2L) = sqrt(X 2^E) = sqrt(x) 2^32 2^(E/2) = sq 2^(E/2 - 30)
   se = E / 2 - 30;
 }
@@ -176,19 +199,20 @@ GRNG_BM_HD void sincos_turns(uint64_t x2, uint64_t& c_abs, bool& c_neg, uint64_t
   if (o & 1u) t = (1ull << 50) - t;                 // reflect: angle pi/4 - beta
   const uint32_t j = (uint32_t)(t >> 42);           // 0..256
   const uint64_t h = t & ((1ull << 42) - 1);
-  const uint64_t P = umulhi(h << 14, k2Pi61);       // phi 2^64, phi < 2 pi 2^-11
-  const uint64_t P2 = umulhi(P, P);                 // phi^2 2^64
-  const uint64_t P3 = umulhi(P2, P);
-  const uint64_t P4 = umulhi(P2, P2);               // < 2^31
-  const uint64_t P5 = umulhi(P3, P2);               // < 2^23
-  const uint64_t P6 = umulhi(P4, P2);               // < 2^15
+  const uint64_t P = umulhi_apx(h << 14, k2Pi61);   // phi 2^64, phi < 2 pi 2^-11
+  const uint64_t P2 = umulhi_apx(P, P);             // phi^2 2^64, < 2^47.3
+  const uint64_t P3 = umulhi_apx(P2, P);            // < 2^39
+  // the small powers only need ~32 significant bits: 32 x 32 products
+  const uint64_t p2s = P2 >> 17;                    // phi^2 2^47, < 2^30.3
+  const uint64_t P4 = (p2s * p2s) >> 30;            // phi^4 2^64, < 2^31
+  const uint64_t P5 = ((P3 >> 8) * p2s) >> 39;      // phi^5 2^64, < 2^23
+  const uint64_t P6 = (P4 * p2s) >> 47;             // phi^6 2^64, < 2^15
   // sin phi = phi - phi^3/6 + phi^5/120 ; 1 - cos phi = phi^2/2 - phi^4/24 + phi^6/720
-  const uint64_t sphi = P - umulhi(P3, kInv6) + (((uint64_t)(uint32_t)P5 * kInv120_32) >> 32);
-  const uint64_t eps = (P2 >> 1) - (((uint64_t)(uint32_t)P4 * kInv24_32) >> 32) +
-                       (((uint64_t)(uint32_t)P6 * kInv720_32) >> 32);
+  const uint64_t sphi = P - umulhi_apx(P3, kInv6) + ((P5 * kInv120_32) >> 32);
+  const uint64_t eps = (P2 >> 1) - ((P4 * kInv24_32) >> 32) + ((P6 * kInv720_32) >> 32);
   const uint64_t Sj = sint(j), Cj = cost(j);
-  const uint64_t sn = Sj - umulhi(Sj, eps) + umulhi(Cj, sphi);  // sin(alpha + phi) 2^63
-  const uint64_t cs = Cj - umulhi(Cj, eps) - umulhi(Sj, sphi);  // cos(alpha + phi) 2^63
+  const uint64_t sn = Sj - umulhi_apx(Sj, eps) + umulhi_apx(Cj, sphi);  // sin(alpha + phi) 2^63
+  const uint64_t cs = Cj - umulhi_apx(Cj, eps) - umulhi_apx(Sj, sphi);  // cos(alpha + phi) 2^63
   const bool swap = ((o + 1u) & 2u) != 0;           // octants 1, 2, 5, 6
   s_abs = swap ? cs : sn;
   c_abs = swap ? sn : cs;
@@ -231,8 +255,8 @@ GRNG_BM_HD void box_muller(uint64_t x1, uint64_t x2, double& z0, double& z1) {
   neg_log(m1, lm, le);
   sqrt2x(lm, le, sq, se);
   // z = sq 2^se * c 2^-63 = umulhi(sq, c) 2^(se + 1)
-  z0 = assemble(umulhi(sq, c_abs), se + 1, c_neg);
-  z1 = assemble(umulhi(sq, s_abs), se + 1, s_neg);
+  z0 = assemble(umulhi_apx(sq, c_abs), se + 1, c_neg);
+  z1 = assemble(umulhi_apx(sq, s_abs), se + 1, s_neg);
 }
 
 }  // namespace bm64

@@ -50,16 +50,19 @@ struct MrgParams {
   uint32_t x[6];              // state at the call's word offset
 };
 
+// p mod m for the products of one step (p < 2^54): one 64-bit fold of
+// 2^32 = c (mod m), then 32-bit folds of the small remaining carry, then one
+// conditional subtraction.
 __device__ __forceinline__ uint32_t red_m1(uint64_t p) {
-  // p < 2^54: two folds of 2^32 = 209 (mod m1), then one conditional subtract
-  uint64_t t = (p & 0xFFFFFFFFull) + (p >> 32) * (uint64_t)mrg::C1;
-  t = (t & 0xFFFFFFFFull) + (t >> 32) * (uint64_t)mrg::C1;
-  return (uint32_t)(t >= mrg::M1 ? t - mrg::M1 : t);
+  const uint64_t t = (uint64_t)(uint32_t)p + (p >> 32) * (uint64_t)mrg::C1;  // < 2^32 + 2^30
+  const uint32_t u = (uint32_t)t + (uint32_t)(t >> 32) * mrg::C1;          // < 2^32
+  return u >= mrg::M1 ? u - mrg::M1 : u;
 }
 __device__ __forceinline__ uint32_t red_m2(uint64_t p) {
-  uint64_t t = (p & 0xFFFFFFFFull) + (p >> 32) * (uint64_t)mrg::C2;
-  t = (t & 0xFFFFFFFFull) + (t >> 32) * (uint64_t)mrg::C2;
-  return (uint32_t)(t >= mrg::M2 ? t - mrg::M2 : t);
+  const uint64_t t = (uint64_t)(uint32_t)p + (p >> 32) * (uint64_t)mrg::C2;  // < 2^32 + 2^37
+  const uint64_t u = (uint64_t)(uint32_t)t + (t >> 32) * (uint64_t)mrg::C2;  // < 2^32 + 2^20
+  const uint32_t v = (uint32_t)u + (uint32_t)(u >> 32) * mrg::C2;          // < 2^32
+  return v >= mrg::M2 ? v - mrg::M2 : v;
 }
 
 struct MrgRegs {
