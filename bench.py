@@ -198,6 +198,36 @@ def oracle_rate(seconds_per_case: float, cores: int, n_cap: int):
     return rates, detail
 
 
+# 32x32 -> 64-bit products per output sample, counted from the algorithms:
+# Philox4x32-10 is 20 products per 4-word block; an MRG32k3a step is 2
+# products per component; the fixed-point FP64 Box-Muller pair is 82 products
+# (24 three-product high multiplies, two exact 64x32 products, 6 small
+# 32-bit products) on top of the products of its 4 words.
+PRODUCTS_PER_SAMPLE = {
+    "philox4x32_10/bits_u32": 5, "philox4x32_10/uniform_f32": 5,
+    "philox4x32_10/uniform_f64": 10, "philox4x32_10/gaussian_f32": 5,
+    "philox4x32_10/gaussian_f64": (20 + 82) / 2, "philox4x32_10/lognormal_f32": 5,
+    "mrg32k3a/bits_u32": 4, "mrg32k3a/uniform_f32": 4, "mrg32k3a/uniform_f64": 8,
+    "mrg32k3a/gaussian_f32": 4, "mrg32k3a/gaussian_f64": (16 + 82) / 2,
+    "mrg32k3a/lognormal_f32": 4,
+}
+
+
+def probe_ceilings(buf_ptr: int, nbytes: int, sink_ptr: int):
+    """Write-only bandwidth and the 32x32->64 product rate on this GPU."""
+    path = os.path.join(ROOT, "paper_2109_01329_gb300", "libgrng_probes.so")
+    lib = ctypes.CDLL(path)
+    lib.grng_probe_write_gbs.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double)]
+    lib.grng_probe_mulwide_rate.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    w, m = ctypes.c_double(), ctypes.c_double()
+    if lib.grng_probe_write_gbs(ctypes.c_void_p(buf_ptr), nbytes, 5, ctypes.byref(w)) != 0:
+        raise RuntimeError("write probe failed")
+    if lib.grng_probe_mulwide_rate(ctypes.c_void_p(sink_ptr), ctypes.byref(m)) != 0:
+        raise RuntimeError("multiply probe failed")
+    return w.value, m.value
+
+
 def aggregate_rate(rates: dict, n: int) -> float:
     """Samples/s for the whole sweep step (n samples per case) at per-case rates."""
     total_t = sum(n / r for r in rates.values())
@@ -333,20 +363,41 @@ def run_ours(args):
     samples_per_step = n * len(cases) * world
     value = samples_per_step / (ms_per_step * 1e-3) / 1e9
 
+    # ceilings measured live on this GPU (outside the timed region)
+    sink = torch.zeros(16, dtype=torch.int32, device=dev)
+    write_gbs, mul_rate = probe_ceilings(buf.data_ptr(), buf.numel(), sink.data_ptr())
     per_kernel = {}
     for i, (ek, en, (name, kind, dtype, p0, p1)) in enumerate(cases):
+        key = f"{en}/{name}"
         ms = statistics.median(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
         es = 8 if dtype == 2 else 4
         gbs = n * es / (ms * 1e-3) / 1e9
-        per_kernel[f"{en}/{name}"] = {"ms": round(ms, 4), "gsamples_s": round(n / ms / 1e6, 2),
-                                      "write_gbs": round(gbs, 1),
-                                      "frac_hbm": round(gbs / hbm_peak, 4)}
+        prods = PRODUCTS_PER_SAMPLE[key] * n
+        tops = prods / (ms * 1e-3) / 1e12
+        # roofline = min(HBM bound, product-rate bound), in samples/s
+        hbm_cap = hbm_peak * 1e9 / es
+        int_cap = mul_rate / PRODUCTS_PER_SAMPLE[key]
+        bound = "hbm" if hbm_cap <= int_cap else "alu"
+        per_kernel[key] = {"ms": round(ms, 4), "gsamples_s": round(n / ms / 1e6, 2),
+                           "write_gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4),
+                           "products_per_launch": prods, "tproducts_s": round(tops, 3),
+                           "frac_int": round(tops * 1e12 / mul_rate, 4),
+                           "bound": bound,
+                           "frac_roofline": round((n / (ms * 1e-3)) / min(hbm_cap, int_cap), 4)}
     dom_name = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     dom = per_kernel[dom_name]
-    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": dom["write_gbs"],
-                "peak": hbm_peak, "unit": "GB/s", "frac": dom["frac_hbm"],
-                "traffic": args.traffic, "peak_source": f"{peak_src} hbm_gbs (copy)",
-                "bytes_per_launch": n * (8 if "f64" in dom_name else 4)}
+    if dom["bound"] == "hbm":
+        roofline = {"kernel": dom_name, "bound": "hbm", "achieved": dom["write_gbs"],
+                    "peak": hbm_peak, "unit": "GB/s", "frac": dom["frac_hbm"],
+                    "traffic": args.traffic, "peak_source": f"{peak_src} hbm_gbs (copy)",
+                    "bytes_per_launch": n * (8 if "f64" in dom_name else 4)}
+    else:
+        roofline = {"kernel": dom_name, "bound": "alu", "achieved": dom["tproducts_s"],
+                    "peak": round(mul_rate / 1e12, 3), "unit": "T products/s (32x32->64)",
+                    "frac": dom["frac_int"], "traffic": args.traffic,
+                    "peak_source": "measured live: dependent 32x32->64 multiply chains, all SMs",
+                    "products_per_launch": dom["products_per_launch"],
+                    "bytes_per_launch": n * (8 if "f64" in dom_name else 4)}
     target = per_kernel.get("philox4x32_10/uniform_f32", dom)
 
     # cuRAND on the same fills (generate calls only; generator created outside)
@@ -439,7 +490,10 @@ def run_ours(args):
             "roofline": roofline,
             "target_philox_uniform_f32": {"write_gbs": target["write_gbs"],
                                           "frac": target["frac_hbm"],
+                                          "frac_roofline": target["frac_roofline"],
                                           "gsamples_s": target["gsamples_s"]},
+            "ceilings": {"hbm_copy_gbs": hbm_peak, "write_only_gbs": round(write_gbs, 1),
+                         "products_per_s": mul_rate},
             "per_kernel": per_kernel, "curand": curand, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": args.steps * len(cases)}
     if rank == 0:

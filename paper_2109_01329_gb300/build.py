@@ -19,6 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libgrng.so")
+PROBES_PATH = os.path.join(HERE, "libgrng_probes.so")
 
 SOURCES = ["capi.cpp", "philox_kernels.cu", "mrg_kernels.cu", "static_stage.cu",
            "transform_kernels.cu"]
@@ -43,10 +44,10 @@ def _flags(ptxas_verbose: bool) -> list[str]:
 
 
 def _needs_build() -> bool:
-    if not os.path.exists(LIB_PATH):
+    if not os.path.exists(LIB_PATH) or not os.path.exists(PROBES_PATH):
         return True
     t = os.path.getmtime(LIB_PATH)
-    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS]
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS + ["probes.cu"]]
     deps.append(os.path.join(INCLUDE, "grng.h"))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps)
@@ -78,6 +79,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB_PATH)
+    # measurement probes (roofline ceilings for bench.py), a separate library
+    pobj = compile_one("probes.cu")
+    tmp = PROBES_PATH + f".tmp{os.getpid()}"
+    r = subprocess.run([cc, "-shared"] + ARCH + ["-cudart", "static", "-o", tmp, pobj],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"probe link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBES_PATH)
     return LIB_PATH
 
 

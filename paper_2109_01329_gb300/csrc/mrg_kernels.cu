@@ -155,7 +155,22 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
 
   uint32_t* row = &stage[warp][lane][0];
   const int64_t nsub = p.chunk_units / kSu;
-  char* out_base = reinterpret_cast<char*>(p.out);
+  uint32_t* out_words = reinterpret_cast<uint32_t*>(p.out);
+  // Aligned copy-out: lane copies 16-byte piece (lane & 7) of rows
+  // it * 4 + (lane >> 3), it = 0..7.  The host makes chunks_per_stream a
+  // multiple of 32 when there are several streams, so the 32 chunks of a
+  // warp lie in one stream and row r is chunk cw + r of that stream.
+  const int64_t cw = ((int64_t)blockIdx.x * kThreads + warp * 32);  // warp's first chunk id
+  const int64_t sw = cw / p.chunks_per_stream;
+  const int64_t cw_in = cw - sw * p.chunks_per_stream;
+  const int64_t lim_chunks = (sw + 1) * p.chunks_per_stream < p.total_chunks
+                                 ? (sw + 1) * p.chunks_per_stream
+                                 : p.total_chunks;
+  const int rows_active = (int)((lim_chunks - cw) < 32 ? (lim_chunks - cw) : 32);
+  const int64_t row_stride = 4 * p.chunk_units * kWpu;  // words between rows it and it + 1
+  const int64_t ow_lane =
+      ((cw_in + (lane >> 3)) * p.chunk_units - p.head_units) * kWpu + (lane & 7) * 4;
+  uint32_t* stream_out = out_words + sw * p.out_words;
   for (int64_t q = 0; q < nsub; ++q) {
     const int64_t ub = u_first + q * kSu;  // first unit of this sub-chunk
     if (active) {
@@ -170,31 +185,24 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
       }
     }
     __syncwarp();
-    const uint32_t s_lo = (uint32_t)s, s_hi = (uint32_t)((uint64_t)s >> 32);
-    const uint32_t ub_lo = (uint32_t)ub, ub_hi = (uint32_t)((uint64_t)ub >> 32);
     if constexpr (kAligned) {
 #pragma unroll
       for (int it = 0; it < 8; ++it) {
         const int r = it * 4 + (lane >> 3);
-        const int piece = lane & 7;
-        const bool r_active = __shfl_sync(0xFFFFFFFFu, active ? 1 : 0, r) != 0;
-        const int64_t r_s = (int64_t)(((uint64_t)__shfl_sync(0xFFFFFFFFu, s_hi, r) << 32) |
-                                      __shfl_sync(0xFFFFFFFFu, s_lo, r));
-        const int64_t r_ub = (int64_t)(((uint64_t)__shfl_sync(0xFFFFFFFFu, ub_hi, r) << 32) |
-                                       __shfl_sync(0xFFFFFFFFu, ub_lo, r));
-        if (!r_active) continue;
-        const int64_t ow = r_ub * kWpu + piece * 4;  // output word within the stream
-        uint32_t* dst = reinterpret_cast<uint32_t*>(out_base) + r_s * p.out_words + ow;
-        const uint32_t* src = &stage[warp][r][piece * 4];
+        if (r >= rows_active) continue;
+        const int64_t ow = ow_lane + it * row_stride + q * kRowWords;
+        const uint32_t* src = &stage[warp][r][(lane & 7) * 4];
         if (ow >= 0 && ow + 4 <= p.out_words) {
-          store16(dst, make_uint4(src[0], src[1], src[2], src[3]));
+          store16(stream_out + ow, make_uint4(src[0], src[1], src[2], src[3]));
         } else {
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            if (ow + i >= 0 && ow + i < p.out_words) dst[i] = src[i];
+            if (ow + i >= 0 && ow + i < p.out_words) stream_out[ow + i] = src[i];
         }
       }
     } else {
+      const uint32_t s_lo = (uint32_t)s, s_hi = (uint32_t)((uint64_t)s >> 32);
+      const uint32_t ub_lo = (uint32_t)ub, ub_hi = (uint32_t)((uint64_t)ub >> 32);
       for (int r = 0; r < 32; ++r) {
         const bool r_active = __shfl_sync(0xFFFFFFFFu, active ? 1 : 0, r) != 0;
         const int64_t r_s = (int64_t)(((uint64_t)__shfl_sync(0xFFFFFFFFu, s_hi, r) << 32) |
@@ -203,8 +211,7 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
                                        __shfl_sync(0xFFFFFFFFu, ub_lo, r));
         if (!r_active) continue;
         const int64_t ow = r_ub * kWpu + lane;
-        if (ow >= 0 && ow < p.out_words)
-          reinterpret_cast<uint32_t*>(out_base)[r_s * p.out_words + ow] = stage[warp][r][lane];
+        if (ow >= 0 && ow < p.out_words) out_words[r_s * p.out_words + ow] = stage[warp][r][lane];
       }
     }
     __syncwarp();
@@ -242,8 +249,16 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
   int64_t cu = (span + per_stream_threads - 1) / per_stream_threads;
   if (cu < 2 * kSu) cu = 2 * kSu;
   cu = (cu + kSu - 1) / kSu * kSu;
+  int64_t cps = (span + cu - 1) / cu;
+  if (r.num_streams > 1) {
+    // a multiple of 32 chunks per stream keeps each warp's 32 chunks inside
+    // one stream; the units are spread over all of them
+    cps = (cps + 31) / 32 * 32;
+    cu = (span + cps - 1) / cps;
+    cu = (cu + kSu - 1) / kSu * kSu;
+  }
   p.chunk_units = cu;
-  p.chunks_per_stream = (span + cu - 1) / cu;
+  p.chunks_per_stream = cps;
   p.total_chunks = p.chunks_per_stream * r.num_streams;
   const int64_t grid = (p.total_chunks + kThreads - 1) / kThreads;
   if (grid > 0x7FFFFFFF) {

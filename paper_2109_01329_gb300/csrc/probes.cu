@@ -1,0 +1,88 @@
+// Ceiling probes for the roofline of the fill kernels (measurement only; not
+// part of the generation path and not declared in grng.h).
+//
+//   grng_probe_write_gbs: write-only HBM bandwidth of a plain 16-byte store
+//     kernel over a caller buffer (the memory ceiling of a fill, which only
+//     writes).
+//   grng_probe_mulwide_rate: 32x32 -> 64-bit products per second, the
+//     operation that bounds Philox rounds, MRG32k3a steps and the fixed-point
+//     FP64 Box-Muller.  Each thread runs 8 independent chains of products
+//     whose results feed the next round, as in a Philox round.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace {
+
+__global__ void __launch_bounds__(256) probe_store(uint4* out, int64_t n16) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n16; j += stride)
+    out[j] = make_uint4((uint32_t)j, 0u, 0u, 0u);
+}
+
+__global__ void __launch_bounds__(256) probe_mulwide(uint32_t* sink, int iters, uint32_t seed) {
+  uint32_t a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = seed + threadIdx.x * 8u + (uint32_t)k + blockIdx.x;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint64_t p = (uint64_t)a[k] * 0xD2511F53u;
+      a[k] = (uint32_t)(p >> 32) ^ (uint32_t)p;
+    }
+  }
+  uint32_t x = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x ^= a[k];
+  if (x == 0x9E3779B9u) sink[0] = x;  // keeps the chains alive
+}
+
+}  // namespace
+
+extern "C" __attribute__((visibility("default"))) int grng_probe_write_gbs(void* dev_buf,
+                                                                             int64_t bytes,
+                                                                             int reps,
+                                                                             double* gbs) {
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 4;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t n16 = bytes / 16;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int grid = sms * 16;
+  for (int i = 0; i < 2; ++i) probe_store<<<grid, 256>>>((uint4*)dev_buf, n16);
+  cudaEventRecord(a);
+  for (int i = 0; i < reps; ++i) probe_store<<<grid, 256>>>((uint4*)dev_buf, n16);
+  cudaEventRecord(b);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *gbs = (double)n16 * 16.0 * reps / (ms * 1e-3) / 1e9;
+  return cudaGetLastError() == cudaSuccess ? 0 : 4;
+}
+
+extern "C" __attribute__((visibility("default"))) int grng_probe_mulwide_rate(void* dev_sink,
+                                                                                double* per_s) {
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 4;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = sms * 8, iters = 4096;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  probe_mulwide<<<grid, 256>>>((uint32_t*)dev_sink, iters, 1u);
+  cudaEventRecord(a);
+  const int reps = 5;
+  for (int i = 0; i < reps; ++i) probe_mulwide<<<grid, 256>>>((uint32_t*)dev_sink, iters, 2u + i);
+  cudaEventRecord(b);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *per_s = (double)grid * 256.0 * iters * 8.0 * reps / (ms * 1e-3);
+  return cudaGetLastError() == cudaSuccess ? 0 : 4;
+}
