@@ -198,18 +198,20 @@ def oracle_rate(seconds_per_case: float, cores: int, n_cap: int):
     return rates, detail
 
 
-# 32x32 -> 64-bit products per output sample, counted from the algorithms:
-# Philox4x32-10 is 20 products per 4-word block; an MRG32k3a step is 2
-# products per component; the fixed-point FP64 Box-Muller pair is 82 products
-# (24 three-product high multiplies, two exact 64x32 products, 6 small
-# 32-bit products) on top of the products of its 4 words.
+# 32x32 -> 64-bit products per output sample, counted from the algorithms as
+# implemented: Philox4x32-10 is 20 products per 4-word block; an MRG32k3a word
+# is 9 (per component two multiplier products, then the folds of 2^32 = c
+# mod m: one wide fold and one carry fold for m1, two wide folds and one
+# carry fold for m2); the fixed-point FP64 Box-Muller pair is 82 products
+# (24 three-product high multiplies, two exact 64x32 products, 6 small 32-bit
+# products) on top of the products of its 4 words.
 PRODUCTS_PER_SAMPLE = {
     "philox4x32_10/bits_u32": 5, "philox4x32_10/uniform_f32": 5,
     "philox4x32_10/uniform_f64": 10, "philox4x32_10/gaussian_f32": 5,
     "philox4x32_10/gaussian_f64": (20 + 82) / 2, "philox4x32_10/lognormal_f32": 5,
-    "mrg32k3a/bits_u32": 4, "mrg32k3a/uniform_f32": 4, "mrg32k3a/uniform_f64": 8,
-    "mrg32k3a/gaussian_f32": 4, "mrg32k3a/gaussian_f64": (16 + 82) / 2,
-    "mrg32k3a/lognormal_f32": 4,
+    "mrg32k3a/bits_u32": 9, "mrg32k3a/uniform_f32": 9, "mrg32k3a/uniform_f64": 18,
+    "mrg32k3a/gaussian_f32": 9, "mrg32k3a/gaussian_f64": (36 + 82) / 2,
+    "mrg32k3a/lognormal_f32": 9,
 }
 
 
