@@ -236,6 +236,74 @@ def aggregate_rate(rates: dict, n: int) -> float:
     return len(rates) * n / total_t
 
 
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(q / 100.0 * (len(xs) - 1))))]
+
+
+def run_batched(grng, torch, dev, reps):
+    """Config 4: 4096 Philox engines (seeds 1..4096), log-uniform sizes in
+    [64, 2^20], five distributions; one graph-replayed persistent launch vs
+    one grng_generate launch per request (back to back on one stream)."""
+    table = W.batched_requests(4096)
+    tdt = {0: torch.int32, 1: torch.float32, 2: torch.float64}
+    reqs, total = [], 0
+    for q in table:
+        name, kind, dtype, p0, p1 = q["dist"]
+        out = torch.empty(q["n"], dtype=tdt[dtype], device=dev)
+        reqs.append((grng.Engine(0, q["seed"], 0), grng.Distribution(kind, dtype, p0, p1), out,
+                     q["n"]))
+        total += q["n"]
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        # per-request launches: each request is its own grng_generate call
+        def loop():
+            for e, d, o, n in reqs:
+                grng.generate(d, e, o, n=n, stream=stream)
+        for _ in range(3):
+            loop()
+        loop_ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            loop()
+            e1.record(stream)
+            e1.synchronize()
+            loop_ms.append(e0.elapsed_time(e1))
+        b = grng.Batch(reqs, ipt=4, stream=stream)
+        ctas, tune_ms = b.autotune(stream=stream)
+        b.launch(stream=stream)
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            b.launch(stream=stream)
+        for _ in range(3):
+            graph.replay()
+        batch_ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            e1.synchronize()
+            batch_ms.append(e0.elapsed_time(e1))
+    med_loop, med_batch = statistics.median(loop_ms), statistics.median(batch_ms)
+    out_bytes = sum(o.numel() * o.element_size() for _, _, o, _ in reqs)
+    return {"workload": "4096 Philox engines (seeds 1..4096), n log-uniform in [64, 2^20], "
+                        "distribution uniform over {bits u32, uniform f32 [0,1), gaussian f32, "
+                        "lognormal f32, uniform f64 [-1,1)}, numpy PCG64 seed 2021",
+            "requests": len(reqs), "samples": total, "bytes": out_bytes,
+            "per_request_ms_p50": round(med_loop, 4), "per_request_ms_p99": round(_pct(loop_ms, 99), 4),
+            "batched_graph_ms_p50": round(med_batch, 4),
+            "batched_graph_ms_p99": round(_pct(batch_ms, 99), 4),
+            "speedup": round(med_loop / med_batch, 3),
+            "batched_gsamples_s": round(total / med_batch / 1e6, 2),
+            "batched_write_gbs": round(out_bytes / med_batch / 1e6, 1),
+            "per_request_gsamples_s": round(total / med_loop / 1e6, 2),
+            "autotune": {"ctas_per_sm": ctas, "ms": round(tune_ms, 4), "ipt": 4},
+            "reps": reps}
+
+
 def run_reference(args):
     """The oracle as the reference arm: bounded samples of the sweep per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -465,6 +533,10 @@ def run_ours(args):
                       "host wall clock"}
         del host, work
 
+    batched = None
+    if rank == 0 and not args.skip_batched:
+        batched = run_batched(grng, torch, dev, args.batch_reps)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         cores = os.cpu_count() or 1
@@ -496,7 +568,8 @@ def run_ours(args):
                                           "gsamples_s": target["gsamples_s"]},
             "ceilings": {"hbm_copy_gbs": hbm_peak, "write_only_gbs": round(write_gbs, 1),
                          "products_per_s": mul_rate},
-            "per_kernel": per_kernel, "curand": curand, "cpu_baseline": cpu, "e2e": e2e,
+            "per_kernel": per_kernel, "curand": curand, "batched": batched,
+            "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": args.steps * len(cases)}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -520,6 +593,8 @@ def main():
     ap.add_argument("--skip-curand", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--batch-reps", type=int, default=20)
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()

@@ -209,6 +209,61 @@ GRNG_API grng_status grng_generate_host(const grng_distribution* dist, grng_engi
                                void* host_ptr, void* dev_work, size_t work_bytes,
                                grng_stream_t stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent requests in one persistent launch: the event batching the
+ * paper names as future work for FastCaloSim (Sec. 6), where per-call
+ * overheads dominate small batches (Sec. 6, Figs. 2-4).  Requests of one
+ * engine follow each other in its sequence in table order, exactly as the
+ * same grng_generate calls would.  Engine state for the batch lives on the
+ * device: every launch fills every request from its current device offset
+ * and then advances each engine by the words of all its requests, so a
+ * replayed launch (for example from a CUDA graph that captured
+ * grng_batch_launch) continues every sequence without host work.
+ * Philox4x32-10 engines only.
+ */
+typedef struct grng_request {
+  grng_engine_t engine;   /* Philox engine; read at grng_batch_create */
+  grng_distribution dist;
+  int64_t n;              /* outputs */
+  void* out;              /* device memory, aligned to the element size */
+} grng_request;
+
+typedef struct grng_batch* grng_batch_t;
+
+/* Device workspace a batch of `count` requests needs with `ipt` 16-byte
+ * groups per thread per tile (1..64); written to *bytes. */
+GRNG_API grng_status grng_batch_workspace_bytes(const grng_request* reqs, int32_t count,
+                                                int32_t ipt, size_t* bytes);
+
+/* Plans the batch and uploads its tables (request records, per-request
+ * offsets, tile map) into dev_workspace (caller-owned, 256-byte aligned, at
+ * least grng_batch_workspace_bytes).  Synchronises `stream` once.  The
+ * engines are read, not advanced (see grng_batch_commit).  The workspace
+ * must stay alive and untouched while the batch exists. */
+GRNG_API grng_status grng_batch_create(grng_batch_t* out, const grng_request* reqs, int32_t count,
+                                       int32_t ipt, void* dev_workspace, size_t workspace_bytes,
+                                       grng_stream_t stream);
+
+/* Enqueues the fill kernel and the offset-advance kernel on `stream`: no host
+ * synchronisation, no allocation; may be captured into a CUDA graph. */
+GRNG_API grng_status grng_batch_launch(grng_batch_t batch, grng_stream_t stream);
+
+/* Times the fill at several CTAs-per-SM settings (without advancing the
+ * offsets: the outputs are rewritten identically) and keeps the fastest;
+ * *best_ctas and *best_ms (either may be NULL) receive the choice. */
+GRNG_API grng_status grng_batch_autotune(grng_batch_t batch, grng_stream_t stream,
+                                         int32_t* best_ctas, float* best_ms);
+
+/* Sets the CTAs-per-SM of the fill (1..32), e.g. from a saved tuning. */
+GRNG_API grng_status grng_batch_set_config(grng_batch_t batch, int32_t ctas_per_sm);
+
+/* Moves each engine of the batch to its device-resident offset (after the
+ * launches so far).  Synchronises `stream`. */
+GRNG_API grng_status grng_batch_commit(grng_batch_t batch, grng_stream_t stream);
+
+/* Releases the plan (not the workspace).  NULL is ignored. */
+GRNG_API grng_status grng_batch_destroy(grng_batch_t batch);
+
 /*
  * Size of the library's static device staging array used by
  * grng_generate_host_static (64 MiB, held on every GPU that loads the

@@ -28,7 +28,9 @@ EXPORTED = ["grng_status_string", "grng_last_error", "grng_engine_create", "grng
             "grng_engine_copy", "grng_engine_skip_ahead", "grng_engine_get_state",
             "grng_engine_destroy", "grng_words_for", "grng_generate",
             "grng_generate_substreams", "grng_generate_host", "grng_generate_host_static",
-            "grng_transform_words"]
+            "grng_transform_words", "grng_batch_workspace_bytes", "grng_batch_create",
+            "grng_batch_launch", "grng_batch_autotune", "grng_batch_set_config",
+            "grng_batch_commit", "grng_batch_destroy"]
 
 
 class GrngError(RuntimeError):
@@ -46,6 +48,11 @@ class _State(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("offset_lo", ctypes.c_uint64),
                 ("offset_hi", ctypes.c_uint64)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("engine", ctypes.c_void_p), ("dist", _Dist), ("n", ctypes.c_int64),
+                ("out", ctypes.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -86,6 +93,16 @@ def load() -> ctypes.CDLL:
         L.grng_generate_host_static.argtypes = [ctypes.POINTER(_Dist), vp, ctypes.c_int64, vp,
                                                 vp]
         L.grng_transform_words.argtypes = [ctypes.POINTER(_Dist), vp, ctypes.c_int64, vp, vp]
+        L.grng_batch_workspace_bytes.argtypes = [ctypes.POINTER(_Request), ctypes.c_int32,
+                                                 ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+        L.grng_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Request),
+                                        ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, vp]
+        L.grng_batch_launch.argtypes = [vp, vp]
+        L.grng_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_float)]
+        L.grng_batch_set_config.argtypes = [vp, ctypes.c_int32]
+        L.grng_batch_commit.argtypes = [vp, vp]
+        L.grng_batch_destroy.argtypes = [vp]
         for name in EXPORTED[2:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -340,3 +357,84 @@ def transform_words(dist: Distribution, words, out, n: int | None = None, stream
                                            ctypes.c_void_p(_stream_ptr(out.device, stream))),
                "grng_transform_words")
     return out
+
+
+class Batch:
+    """A planned batch of requests (grng_batch_*).
+
+    requests: list of (engine, distribution, out_tensor[, n]).  The device
+    workspace is allocated here as a torch tensor and kept alive with the
+    batch.  launch() enqueues the persistent fill and the device-side offset
+    advance (capturable in a CUDA graph); commit() moves the engines to the
+    device-resident offsets.
+    """
+
+    def __init__(self, requests, ipt: int = 4, stream=None):
+        import torch
+
+        self._reqs = list(requests)
+        arr = (_Request * len(self._reqs))()
+        self._keep = []
+        dev = None
+        for i, r in enumerate(self._reqs):
+            engine, dist, out = r[0], r[1], r[2]
+            n = r[3] if len(r) > 3 else out.numel()
+            if not out.is_cuda or not _torch_dtype_ok(out, dist.dtype):
+                raise ValueError(f"request {i}: out must be a CUDA tensor of the dtype")
+            dev = out.device
+            arr[i].engine = engine.handle
+            arr[i].dist = dist._c()
+            arr[i].n = n
+            arr[i].out = out.data_ptr()
+            self._keep.append((engine, out))
+        self._arr = arr
+        L = load()
+        nbytes = ctypes.c_size_t()
+        _check(L.grng_batch_workspace_bytes(arr, len(arr), ipt, ctypes.byref(nbytes)),
+               "grng_batch_workspace_bytes")
+        self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
+        self._dev = dev
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            _check(L.grng_batch_create(ctypes.byref(self._h), arr, len(arr), ipt,
+                                       ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value,
+                                       ctypes.c_void_p(_stream_ptr(dev, stream))),
+                   "grng_batch_create")
+
+    def launch(self, stream=None):
+        import torch
+
+        with torch.cuda.device(self._dev):
+            _check(load().grng_batch_launch(self._h, ctypes.c_void_p(_stream_ptr(self._dev, stream))),
+                   "grng_batch_launch")
+
+    def autotune(self, stream=None):
+        import torch
+
+        c, ms = ctypes.c_int32(), ctypes.c_float()
+        with torch.cuda.device(self._dev):
+            _check(load().grng_batch_autotune(self._h, ctypes.c_void_p(_stream_ptr(self._dev, stream)),
+                                              ctypes.byref(c), ctypes.byref(ms)),
+                   "grng_batch_autotune")
+        return c.value, ms.value
+
+    def set_config(self, ctas_per_sm: int):
+        _check(load().grng_batch_set_config(self._h, ctas_per_sm), "grng_batch_set_config")
+
+    def commit(self, stream=None):
+        import torch
+
+        with torch.cuda.device(self._dev):
+            _check(load().grng_batch_commit(self._h, ctypes.c_void_p(_stream_ptr(self._dev, stream))),
+                   "grng_batch_commit")
+
+    def close(self):
+        if self._h:
+            load().grng_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

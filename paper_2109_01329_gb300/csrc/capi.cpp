@@ -267,6 +267,13 @@ std::mutex g_host_flow_init;
 
 }  // namespace
 
+grng_status fill_transform_params(const grng_distribution* d, TransformParams* t, int* variant) {
+  const grng_status st = check_dist(d);
+  if (st != GRNG_OK) return st;
+  *variant = choose_variant(d, t);
+  return GRNG_OK;
+}
+
 void set_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);

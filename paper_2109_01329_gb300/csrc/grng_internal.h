@@ -77,6 +77,9 @@ grng_status launch_mrg(const FillRequest& r, CUstream_st* stream);
 grng_status launch_transform(int variant, const TransformParams& t, const uint32_t* words,
                              int64_t n, void* out, CUstream_st* stream);
 
+// Checks a distribution and fills the kernels' parameters and variant.
+grng_status fill_transform_params(const grng_distribution* d, TransformParams* t, int* variant);
+
 // Records an error message for grng_last_error() on this thread.
 void set_error(const char* fmt, ...);
 
