@@ -84,6 +84,17 @@ def _expected_starts(g, reqs, meta):
     return starts, pos
 
 
+def _clone_requests(g, reqs):
+    """The same requests on fresh engines with the same sharing and offsets."""
+    fresh = {}
+    out = []
+    for (e, d, o, n) in reqs:
+        if id(e) not in fresh:
+            fresh[id(e)] = g.Engine(0, e.state[1], e.offset)
+        out.append((fresh[id(e)], d, torch.empty_like(o), n))
+    return out
+
+
 def test_batch_equals_oracle_and_continues(g):
     reqs, meta, shared = _mixed_requests(g)
     starts, ends = _expected_starts(g, reqs, meta)
@@ -112,9 +123,7 @@ def test_batch_equals_oracle_and_continues(g):
 
 def test_batch_graph_replay_equals_launches(g):
     reqs_a, meta, _ = _mixed_requests(g, seed=9, count=30)
-    # an identical second set of engines and buffers
-    reqs_b = [(g.Engine(0, e.state[1], e.offset), d, torch.empty_like(o), n)
-              for (e, d, o, n) in reqs_a]
+    reqs_b = _clone_requests(g, reqs_a)
     ba = g.Batch(reqs_a, ipt=4)
     bb = g.Batch(reqs_b, ipt=4)
     s = torch.cuda.Stream()
@@ -143,8 +152,7 @@ def test_autotune_keeps_outputs(g):
     torch.cuda.synchronize()
     before = [r[2].clone() for r in reqs]
     # rewind: a fresh identical batch tuned then launched once
-    reqs2 = [(g.Engine(0, e.state[1], e.offset), d, torch.empty_like(o), n)
-             for (e, d, o, n) in reqs]
+    reqs2 = _clone_requests(g, reqs)
     b2 = g.Batch(reqs2, ipt=1)
     ctas, ms = b2.autotune()
     assert 1 <= ctas <= 32 and ms > 0
