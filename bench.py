@@ -304,6 +304,41 @@ def run_batched(grng, torch, dev, reps):
             "reps": reps}
 
 
+def run_serving(grng, torch, dev, seconds, stress):
+    """Config 5: FastCaloSim-shaped serving.  Poisson arrivals at 2000 events/s,
+    hits ~ lognormal(mean 8000, sigma 0.8) clipped to [100, 200000]; each event
+    = 3h FP32 uniforms + h FP32 gaussians from its own Philox engine (seed =
+    event id); 4 GB admission budget; replayed in real time, then compressed
+    `stress` times so that the budget and the backlog bind."""
+    t, hits = W.fastcalosim_events(rate_hz=2000.0, duration_s=seconds, seed=2021)
+    u = grng.Distribution.uniform(0.0, 1.0, grng.F32)
+    z = grng.Distribution.gaussian(0.0, 1.0, grng.F32)
+    reqs = [grng.serve_request(i + 1, [(u, 3 * int(h)), (z, int(h))]) for i, h in enumerate(hits)]
+    out = {"workload": f"Poisson 2000 events/s for {seconds:g} s ({len(reqs)} events), hits "
+                       "lognormal mean 8000 sigma 0.8 clipped [100, 2e5], 3h uniform f32 + h "
+                       "gaussian f32 per event from Philox seed = event id, 4 GB budget, "
+                       "3 stream slots",
+           "events": len(reqs), "samples": int(4 * hits.sum())}
+    srv = grng.Server(4 << 30, num_streams=3, auto_release=True, device=dev)
+    for name, scale in (("real_time", 1.0), (f"stress_{stress:g}x", 1.0 / stress)):
+        srv.reset_stats()
+        srv.replay(t, reqs, time_scale=scale)
+        srv.drain(timeout_s=600)
+        st = srv.stats()
+        out[name] = {"gsamples_s": round(st["samples"] / st["wall_s"] / 1e9, 3) if st["wall_s"]
+                     else None,
+                     "latency_p50_us": round(st["latency_p50_us"], 1),
+                     "latency_p99_us": round(st["latency_p99_us"], 1),
+                     "latency_max_us": round(st["latency_max_us"], 1),
+                     "completed": st["completed"], "rejected": st["rejected"],
+                     "batches": st["batches"],
+                     "mean_batch_events": round(st["mean_batch_requests"], 2),
+                     "peak_pool_gb": round(st["peak_pool_bytes"] / 1e9, 3),
+                     "wall_s": round(st["wall_s"], 3)}
+    srv.close()
+    return out
+
+
 def run_reference(args):
     """The oracle as the reference arm: bounded samples of the sweep per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -537,6 +572,10 @@ def run_ours(args):
     if rank == 0 and not args.skip_batched:
         batched = run_batched(grng, torch, dev, args.batch_reps)
 
+    serving = None
+    if rank == 0 and args.serve_seconds > 0:
+        serving = run_serving(grng, torch, dev, args.serve_seconds, args.serve_stress)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         cores = os.cpu_count() or 1
@@ -568,7 +607,7 @@ def run_ours(args):
                                           "gsamples_s": target["gsamples_s"]},
             "ceilings": {"hbm_copy_gbs": hbm_peak, "write_only_gbs": round(write_gbs, 1),
                          "products_per_s": mul_rate},
-            "per_kernel": per_kernel, "curand": curand, "batched": batched,
+            "per_kernel": per_kernel, "curand": curand, "batched": batched, "serving": serving,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": args.steps * len(cases)}
     if rank == 0:
@@ -595,6 +634,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--batch-reps", type=int, default=20)
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="seconds of the arrival trace to replay in real time (0: skip)")
+    ap.add_argument("--serve-stress", type=float, default=20.0)
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()

@@ -264,6 +264,85 @@ GRNG_API grng_status grng_batch_commit(grng_batch_t batch, grng_stream_t stream)
 /* Releases the plan (not the workspace).  NULL is ignored. */
 GRNG_API grng_status grng_batch_destroy(grng_batch_t batch);
 
+/* ------------------------------------------------------------------ serving
+ * A continuous-batching server for FastCaloSim-shaped demand (Sec. 4.2: each
+ * event needs three uniforms per calorimeter hit, thousands of hits; Sec. 6
+ * names event batching as the way to use the GPU).  Requests arrive at any
+ * time; a scheduler thread admits them in arrival order while their outputs
+ * fit a device-memory budget, packs the admitted ones into one batched
+ * launch per free stream slot, and stamps each request complete from a host
+ * callback.  Batches on different streams overlap on the device.
+ */
+#define GRNG_SERVE_AUTO_RELEASE 1 /* free outputs at completion (throughput runs) */
+
+typedef struct grng_serve_part {
+  grng_distribution dist;
+  int64_t n;
+} grng_serve_part;
+
+/* One request: up to four parts drawn in turn from one Philox4x32-10 engine
+ * (key = seed, first part at word offset offset_lo + 2^64 offset_hi, each
+ * next part after the words of the previous ones).  The output buffer holds
+ * the parts one after another, each aligned to its element size. */
+typedef struct grng_serve_request {
+  uint64_t seed;
+  uint64_t offset_lo, offset_hi;
+  int32_t num_parts; /* 1..4 */
+  int32_t reserved;
+  grng_serve_part parts[4];
+} grng_serve_request;
+
+typedef struct grng_serve_stats {
+  int64_t submitted, completed, rejected, samples, batches;
+  double wall_s;             /* first arrival to last completion */
+  double latency_p50_us, latency_p90_us, latency_p99_us, latency_max_us, latency_mean_us;
+  double peak_pool_bytes;    /* high-water mark of admitted output bytes */
+  double mean_batch_requests;
+} grng_serve_stats;
+
+typedef struct grng_server* grng_server_t;
+
+/* Creates a server over the caller's device pool (256-byte aligned; batch
+ * tables for each stream slot take ~1.7 MB at its start, the rest is the
+ * output budget).  num_streams: 1..8 stream slots.  flags:
+ * GRNG_SERVE_AUTO_RELEASE or 0.  Starts the scheduler thread.  The pool must
+ * outlive the server. */
+GRNG_API grng_status grng_server_create(grng_server_t* out, void* dev_pool, size_t pool_bytes,
+                                        int32_t num_streams, int32_t flags);
+
+/* Queues a request and returns at once with its ticket.  BUDGET if the
+ * request alone can never fit the budget; INVALID_ARG for a bad request. */
+GRNG_API grng_status grng_server_submit(grng_server_t server, const grng_serve_request* req,
+                                        uint64_t* ticket);
+
+/* Waits up to timeout_us for a request; on completion *dev_out / *bytes
+ * (either may be NULL) locate its output in the pool.  TIMEOUT if not done. */
+GRNG_API grng_status grng_server_wait(grng_server_t server, uint64_t ticket, int64_t timeout_us,
+                                      void** dev_out, size_t* bytes);
+
+/* Returns a completed request's output space to the budget. */
+GRNG_API grng_status grng_server_release(grng_server_t server, uint64_t ticket);
+
+/* Waits up to timeout_us until nothing is queued or running. */
+GRNG_API grng_status grng_server_drain(grng_server_t server, int64_t timeout_us);
+
+/* Counters and arrival-to-completion latency percentiles since creation or
+ * the last reset. */
+GRNG_API grng_status grng_server_stats(grng_server_t server, grng_serve_stats* out);
+GRNG_API grng_status grng_server_reset_stats(grng_server_t server);
+
+/* Submits reqs[i] at arrival_s[i] * time_scale seconds after the call (a
+ * trace replay driven from the calling thread); returns after the last
+ * submission.  Requests that can never fit are counted as rejected. */
+GRNG_API grng_status grng_server_replay(grng_server_t server, const double* arrival_s,
+                                        const grng_serve_request* reqs, int64_t count,
+                                        double time_scale);
+
+/* Stops the scheduler (requests not yet launched are abandoned), waits for
+ * the running batches and releases the server.  Drain first to finish
+ * everything submitted.  NULL is ignored. */
+GRNG_API grng_status grng_server_destroy(grng_server_t server);
+
 /*
  * Size of the library's static device staging array used by
  * grng_generate_host_static (64 MiB, held on every GPU that loads the

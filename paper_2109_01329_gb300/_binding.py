@@ -30,7 +30,10 @@ EXPORTED = ["grng_status_string", "grng_last_error", "grng_engine_create", "grng
             "grng_generate_substreams", "grng_generate_host", "grng_generate_host_static",
             "grng_transform_words", "grng_batch_workspace_bytes", "grng_batch_create",
             "grng_batch_launch", "grng_batch_autotune", "grng_batch_set_config",
-            "grng_batch_commit", "grng_batch_destroy"]
+            "grng_batch_commit", "grng_batch_destroy", "grng_server_create",
+            "grng_server_submit", "grng_server_wait", "grng_server_release", "grng_server_drain",
+            "grng_server_stats", "grng_server_reset_stats", "grng_server_replay",
+            "grng_server_destroy"]
 
 
 class GrngError(RuntimeError):
@@ -53,6 +56,26 @@ class _State(ctypes.Structure):
 class _Request(ctypes.Structure):
     _fields_ = [("engine", ctypes.c_void_p), ("dist", _Dist), ("n", ctypes.c_int64),
                 ("out", ctypes.c_void_p)]
+
+
+class _ServePart(ctypes.Structure):
+    _fields_ = [("dist", _Dist), ("n", ctypes.c_int64)]
+
+
+class _ServeRequest(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("offset_lo", ctypes.c_uint64),
+                ("offset_hi", ctypes.c_uint64), ("num_parts", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("parts", _ServePart * 4)]
+
+
+class _ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("samples", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("wall_s", ctypes.c_double),
+                ("latency_p50_us", ctypes.c_double), ("latency_p90_us", ctypes.c_double),
+                ("latency_p99_us", ctypes.c_double), ("latency_max_us", ctypes.c_double),
+                ("latency_mean_us", ctypes.c_double), ("peak_pool_bytes", ctypes.c_double),
+                ("mean_batch_requests", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -103,6 +126,20 @@ def load() -> ctypes.CDLL:
         L.grng_batch_set_config.argtypes = [vp, ctypes.c_int32]
         L.grng_batch_commit.argtypes = [vp, vp]
         L.grng_batch_destroy.argtypes = [vp]
+        L.grng_server_create.argtypes = [ctypes.POINTER(vp), vp, ctypes.c_size_t, ctypes.c_int32,
+                                         ctypes.c_int32]
+        L.grng_server_submit.argtypes = [vp, ctypes.POINTER(_ServeRequest),
+                                         ctypes.POINTER(ctypes.c_uint64)]
+        L.grng_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(vp),
+                                       ctypes.POINTER(ctypes.c_size_t)]
+        L.grng_server_release.argtypes = [vp, ctypes.c_uint64]
+        L.grng_server_drain.argtypes = [vp, ctypes.c_int64]
+        L.grng_server_stats.argtypes = [vp, ctypes.POINTER(_ServeStats)]
+        L.grng_server_reset_stats.argtypes = [vp]
+        L.grng_server_replay.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(_ServeRequest), ctypes.c_int64,
+                                         ctypes.c_double]
+        L.grng_server_destroy.argtypes = [vp]
         for name in EXPORTED[2:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -431,6 +468,91 @@ class Batch:
     def close(self):
         if self._h:
             load().grng_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+SERVE_AUTO_RELEASE = 1
+
+
+def serve_request(seed: int, parts, offset: int = 0) -> _ServeRequest:
+    """A server request: parts = [(Distribution, n), ...] (1..4) from one Philox engine."""
+    if not 1 <= len(parts) <= 4:
+        raise ValueError("1 to 4 parts")
+    q = _ServeRequest()
+    q.seed = seed % (1 << 64)
+    q.offset_lo, q.offset_hi = _split128(offset)
+    q.num_parts = len(parts)
+    for k, (d, n) in enumerate(parts):
+        q.parts[k].dist = d._c()
+        q.parts[k].n = n
+    return q
+
+
+class Server:
+    """Continuous-batching server (grng_server_*) over a device pool tensor."""
+
+    def __init__(self, pool_bytes: int, num_streams: int = 2, auto_release: bool = False,
+                 device=None):
+        import torch
+
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        self.pool = torch.empty(pool_bytes, dtype=torch.uint8, device=self.device)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(load().grng_server_create(ctypes.byref(self._h),
+                                             ctypes.c_void_p(self.pool.data_ptr()), pool_bytes,
+                                             num_streams, SERVE_AUTO_RELEASE if auto_release else 0),
+                   "grng_server_create")
+
+    def submit(self, req: _ServeRequest) -> int:
+        t = ctypes.c_uint64()
+        _check(load().grng_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)),
+               "grng_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 30.0):
+        """(device address, bytes) of a completed request's output."""
+        p, b = ctypes.c_void_p(), ctypes.c_size_t()
+        _check(load().grng_server_wait(self._h, ticket, int(timeout_s * 1e6), ctypes.byref(p),
+                                       ctypes.byref(b)), "grng_server_wait")
+        return p.value, b.value
+
+    def output(self, ticket: int, timeout_s: float = 30.0):
+        """The completed request's output bytes as a view of the pool tensor."""
+        addr, nbytes = self.wait(ticket, timeout_s)
+        off = addr - self.pool.data_ptr()
+        return self.pool[off:off + nbytes]
+
+    def release(self, ticket: int) -> None:
+        _check(load().grng_server_release(self._h, ticket), "grng_server_release")
+
+    def drain(self, timeout_s: float = 120.0) -> None:
+        _check(load().grng_server_drain(self._h, int(timeout_s * 1e6)), "grng_server_drain")
+
+    def stats(self) -> dict:
+        s = _ServeStats()
+        _check(load().grng_server_stats(self._h, ctypes.byref(s)), "grng_server_stats")
+        return {k: getattr(s, k) for k, _ in _ServeStats._fields_}
+
+    def reset_stats(self) -> None:
+        _check(load().grng_server_reset_stats(self._h), "grng_server_reset_stats")
+
+    def replay(self, arrivals, requests, time_scale: float = 1.0) -> None:
+        n = len(requests)
+        arr = (ctypes.c_double * n)(*[float(a) for a in arrivals])
+        rq = (_ServeRequest * n)(*requests)
+        _check(load().grng_server_replay(self._h, arr, rq, n, time_scale), "grng_server_replay")
+
+    def close(self) -> None:
+        if self._h:
+            load().grng_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

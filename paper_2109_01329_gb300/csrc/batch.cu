@@ -34,18 +34,6 @@
 
 namespace grng {
 
-struct BatchReq {
-  TransformParams t;
-  uint64_t out;        // device address of element 0
-  int64_t n;           // elements
-  int64_t groups;      // 16-byte groups covering [out, out + n) (with the head)
-  int64_t first_tile;
-  uint64_t adv_lo, adv_hi;  // words the engine advances per launch
-  uint32_t key0, key1;
-  int32_t variant;
-  int32_t head;        // elements of group 0 before out
-};
-
 namespace {
 
 using namespace dev;
@@ -172,6 +160,50 @@ __global__ void batch_advance_kernel(const BatchReq* __restrict__ reqs, uint64_t
 }
 
 }  // namespace
+
+int64_t plan_parts(const PartDesc* parts, int32_t count, int ipt, BatchReq* reqs_out,
+                   uint64_t* offs_out, int32_t* tiles_out, int64_t tile_cap) {
+  const int64_t tile_groups = (int64_t)kThreads * ipt;
+  int64_t t = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    const PartDesc& q = parts[i];
+    BatchReq& r = reqs_out[i];
+    std::memset(&r, 0, sizeof(r));
+    const int64_t epg = 16 / q.es;
+    const int32_t head = (int32_t)((q.out & 15u) / (uint64_t)q.es);
+    const int64_t groups = q.n == 0 ? 0 : (head + q.n + epg - 1) / epg;
+    r.t = q.t;
+    r.out = q.out;
+    r.n = q.n;
+    r.groups = groups;
+    r.first_tile = t;
+    r.variant = q.variant;
+    r.head = head;
+    r.key0 = q.key0;
+    r.key1 = q.key1;
+    offs_out[2 * i] = q.off_lo;
+    offs_out[2 * i + 1] = q.off_hi;
+    const int64_t nt = (groups + tile_groups - 1) / tile_groups;
+    if (t + nt > tile_cap) return -1;
+    for (int64_t k = 0; k < nt; ++k) tiles_out[t + k] = i;
+    t += nt;
+  }
+  return t;
+}
+
+grng_status enqueue_fill(const BatchReq* d_reqs, const uint64_t* d_offs, const int32_t* d_tiles,
+                         int64_t tiles, int ipt, int64_t grid, cudaStream_t stream) {
+  if (tiles <= 0) return GRNG_OK;
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  batch_fill_kernel<<<(unsigned)grid, kThreads, 0, stream>>>(d_reqs, d_offs, d_tiles, tiles, ipt);
+  const cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    set_error("batch fill launch failed: %s", cudaGetErrorString(err));
+    return GRNG_ERR_CUDA;
+  }
+  return GRNG_OK;
+}
 
 }  // namespace grng
 

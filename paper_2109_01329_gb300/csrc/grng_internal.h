@@ -70,6 +70,41 @@ struct FillRequest {
   uint32_t mrg[6];     // MRG32k3a state at word offset off: x1[3], x2[3]
 };
 
+// One request of a batched fill as the device sees it (batch.cu).
+struct BatchReq {
+  TransformParams t;
+  uint64_t out;        // device address of element 0
+  int64_t n;           // elements
+  int64_t groups;      // 16-byte groups covering [out, out + n) (with the head)
+  int64_t first_tile;
+  uint64_t adv_lo, adv_hi;  // words the engine advances per launch
+  uint32_t key0, key1;
+  int32_t variant;
+  int32_t head;        // elements of group 0 before out
+};
+
+// A Philox fill described for plan_parts: key, starting word offset,
+// distribution (variant + parameters), size and device output address.
+struct PartDesc {
+  uint32_t key0, key1;
+  uint64_t off_lo, off_hi;
+  TransformParams t;
+  int variant;
+  int es;              // element size
+  int64_t n;
+  uint64_t out;
+};
+
+// Writes batch records, starting offsets and the tile -> part map for `count`
+// parts (no per-launch advance); returns the number of tiles, or -1 when it
+// would exceed tile_cap.
+int64_t plan_parts(const PartDesc* parts, int32_t count, int ipt, BatchReq* reqs_out,
+                   uint64_t* offs_out, int32_t* tiles_out, int64_t tile_cap);
+
+// Enqueues the batched fill over device copies of those tables.
+grng_status enqueue_fill(const BatchReq* d_reqs, const uint64_t* d_offs, const int32_t* d_tiles,
+                         int64_t tiles, int ipt, int64_t grid, CUstream_st* stream);
+
 // Kernel launchers; return GRNG_OK or GRNG_ERR_CUDA (detail via set_error).
 grng_status launch_philox(const FillRequest& r, CUstream_st* stream);
 grng_status launch_mrg(const FillRequest& r, CUstream_st* stream);

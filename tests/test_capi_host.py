@@ -138,3 +138,36 @@ def test_substream_limits(g):
                                       ctypes.c_void_p(0), None)
     assert st == 0
     assert e.offset == 0
+
+
+def test_server_argument_errors(g):
+    lib = g.load()
+    h = ctypes.c_void_p()
+    # NULL pool, misaligned pool, bad stream counts: refused before any CUDA call
+    assert lib.grng_server_create(ctypes.byref(h), None, 1 << 30, 2, 0) == 1
+    assert lib.grng_server_create(ctypes.byref(h), ctypes.c_void_p(0x1001), 1 << 30, 2, 0) == 1
+    assert lib.grng_server_create(ctypes.byref(h), ctypes.c_void_p(0x1000), 1 << 30, 0, 0) == 1
+    assert lib.grng_server_create(ctypes.byref(h), ctypes.c_void_p(0x1000), 1 << 30, 9, 0) == 1
+    assert lib.grng_server_create(ctypes.byref(h), ctypes.c_void_p(0x1000), 1 << 10, 2, 0) == 1
+    assert lib.grng_server_destroy(None) == 0
+    t = ctypes.c_uint64()
+    assert lib.grng_server_submit(None, None, ctypes.byref(t)) == 1
+
+
+def test_batch_argument_errors(g):
+    lib = g.load()
+    nbytes = ctypes.c_size_t()
+    assert lib.grng_batch_workspace_bytes(None, 1, 4, ctypes.byref(nbytes)) == 1
+    e = g.Engine(g.MRG32K3A, 1, 0)
+    req = (g._binding._Request * 1)()
+    req[0].engine = e.handle
+    req[0].dist = g.Distribution.uniform()._c()
+    req[0].n = 16
+    req[0].out = 0x100000
+    assert lib.grng_batch_workspace_bytes(req, 1, 4, ctypes.byref(nbytes)) == 2  # MRG: unsupported
+    pe = g.Engine(g.PHILOX4X32X10, 1, 0)
+    req[0].engine = pe.handle
+    assert lib.grng_batch_workspace_bytes(req, 1, 4, ctypes.byref(nbytes)) == 0
+    assert nbytes.value >= 256
+    assert lib.grng_batch_workspace_bytes(req, 1, 0, ctypes.byref(nbytes)) == 1  # ipt out of range
+    assert lib.grng_batch_destroy(None) == 0
