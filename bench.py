@@ -320,7 +320,8 @@ def run_serving(grng, torch, dev, seconds, stress):
                        "3 stream slots",
            "events": len(reqs), "samples": int(4 * hits.sum())}
     srv = grng.Server(4 << 30, num_streams=3, auto_release=True, device=dev)
-    for name, scale in (("real_time", 1.0), (f"stress_{stress:g}x", 1.0 / stress)):
+    for name, scale in (("real_time", 1.0), (f"stress_{stress:g}x", 1.0 / stress),
+                        ("burst", 1e-9)):
         srv.reset_stats()
         srv.replay(t, reqs, time_scale=scale)
         srv.drain(timeout_s=600)
@@ -336,6 +337,27 @@ def run_serving(grng, torch, dev, seconds, stress):
                      "peak_pool_gb": round(st["peak_pool_bytes"] / 1e9, 3),
                      "wall_s": round(st["wall_s"], 3)}
     srv.close()
+    # the plain form: two grng_generate launches per event, back to back on one
+    # stream, into one preallocated buffer (no admission, no batching)
+    buf = torch.empty(int(4 * hits.max()), dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for i, h in enumerate(hits):
+            h = int(h)
+            e = grng.Engine(0, i + 1, 0)
+            grng.generate(u, e, buf[:3 * h], stream=stream)
+            grng.generate(z, e, buf[3 * h:4 * h], stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        wall = time.perf_counter() - t0
+    out["per_event_launches"] = {"gsamples_s": round(out["samples"] / wall / 1e9, 3),
+                                 "wall_s": round(wall, 3), "gpu_ms": round(e0.elapsed_time(e1), 3)}
+    if out["burst"]["gsamples_s"]:
+        out["burst_speedup_vs_per_event"] = round(out["burst"]["gsamples_s"] /
+                                                  out["per_event_launches"]["gsamples_s"], 2)
     return out
 
 
