@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "device_common.cuh"
 #include "grng_internal.h"
@@ -35,6 +36,7 @@ using namespace dev;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kRowWords = 32;  // output words per row per sub-chunk (128 bytes)
+constexpr int kJumpLevels = 24;  // per-launch jump tables: up to 2^24 chunks and streams
 
 struct MrgParams {
   TransformParams t;
@@ -48,6 +50,11 @@ struct MrgParams {
   int64_t head_units;         // virtual units before `out` in the first chunk
   uint64_t stride_lo, stride_hi;  // word stride between streams
   uint32_t x[6];              // state at the call's word offset
+  uint32_t x1[6];             // state at the first unit of chunk 1 of stream 0
+  int32_t chunk_levels;       // entries of chunk_tab (0: generic jump)
+  int32_t stream_levels;      // entries of stream_tab
+  uint32_t chunk_tab[kJumpLevels][2][9];   // A^(chunk_units wpu 2^k)
+  uint32_t stream_tab[kJumpLevels][2][9];  // A^(stride 2^k)
 };
 
 // p mod m for the products of one step (p < 2^54): one 64-bit fold of
@@ -86,6 +93,44 @@ __device__ __forceinline__ uint32_t mrg_next(MrgRegs& s) {
   return n1 >= n2 ? n1 - n2 : n1 - n2 + mrg::M1;
 }
 
+// y = M x mod m with one fold per product: each product p < 2^64 becomes
+// (p mod 2^32) + (p >> 32) c < 2^32 (c + 1); three of them sum below 2^49,
+// which two more folds and a conditional subtraction reduce.
+template <uint32_t kM, uint32_t kC>
+__device__ __forceinline__ uint32_t row_mod(const uint32_t* m, const uint32_t* x) {
+  uint64_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint64_t p = (uint64_t)m[k] * x[k];
+    acc += (uint64_t)(uint32_t)p + (uint64_t)(uint32_t)(p >> 32) * kC;
+  }
+  const uint64_t t = (uint64_t)(uint32_t)acc + (uint64_t)(uint32_t)(acc >> 32) * kC;
+  const uint64_t u = (uint64_t)(uint32_t)t + (uint64_t)(uint32_t)(t >> 32) * kC;
+  const uint32_t v = (uint32_t)u + (uint32_t)(u >> 32) * kC;
+  return v >= kM ? v - kM : v;
+}
+
+__device__ __forceinline__ void apply(const uint32_t* m1, const uint32_t* m2, MrgRegs& s) {
+  const uint32_t x1[3] = {s.a0, s.a1, s.a2};
+  const uint32_t x2[3] = {s.b0, s.b1, s.b2};
+  s.a0 = row_mod<mrg::M1, mrg::C1>(m1 + 0, x1);
+  s.a1 = row_mod<mrg::M1, mrg::C1>(m1 + 3, x1);
+  s.a2 = row_mod<mrg::M1, mrg::C1>(m1 + 6, x1);
+  s.b0 = row_mod<mrg::M2, mrg::C2>(m2 + 0, x2);
+  s.b1 = row_mod<mrg::M2, mrg::C2>(m2 + 3, x2);
+  s.b2 = row_mod<mrg::M2, mrg::C2>(m2 + 6, x2);
+}
+
+// Applies table[k] (= A^(unit 2^k), both components) for the set bits of e;
+// the loop over levels is warp-uniform so all lanes read the same entry.
+__device__ __forceinline__ void jump_table(MrgRegs& s, const uint32_t (*tab)[2][9], int levels,
+                                           uint64_t e) {
+  for (int k = 0; k < levels; ++k) {
+    if ((e >> k) & 1u) apply(tab[k][0], tab[k][1], s);
+    if (!__any_sync(0xFFFFFFFFu, (e >> k) > 1u)) break;
+  }
+}
+
 __device__ __forceinline__ void jump(MrgRegs& s, uint64_t e_lo, uint64_t e_hi) {
   uint32_t x1[3] = {s.a0, s.a1, s.a2};
   uint32_t x2[3] = {s.b0, s.b1, s.b2};
@@ -106,24 +151,24 @@ __device__ __forceinline__ void jump(MrgRegs& s, uint64_t e_lo, uint64_t e_hi) {
   s.b0 = x2[0]; s.b1 = x2[1]; s.b2 = x2[2];
 }
 
+// Generates one unit's words and writes its kWpu output words to o.
 template <int V>
-__device__ __forceinline__ void gen_unit(MrgRegs& st, uint32_t* row, int pos,
-                                         const TransformParams& t) {
+__device__ __forceinline__ void gen_unit(MrgRegs& st, uint32_t* o, const TransformParams& t) {
   constexpr int kWpu = VInfo<V>::wpu;
   uint32_t w[kWpu];
 #pragma unroll
   for (int i = 0; i < kWpu; ++i) w[i] = mrg_next(st);
-  uint32_t o[kWpu];
   unit_outputs<V>(w, o, t);
-#pragma unroll
-  for (int i = 0; i < kWpu; ++i) row[pos + i] = o[i];
 }
 
 template <int V, bool kAligned>
 __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
   constexpr int kWpu = VInfo<V>::wpu;
   constexpr int kSu = kRowWords / kWpu;  // units per sub-chunk
-  __shared__ uint32_t stage[kWarps][32][kRowWords + 1];
+  // per warp: 32 rows (one per lane) of 8 16-byte chunks; chunk q of row r is
+  // kept at position q ^ (r & 7), so a lane's chunk stores and the copy-out's
+  // row loads are both free of bank conflicts
+  __shared__ uint4 stage[kWarps][32][8];
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int64_t cid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -136,9 +181,17 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
   const int64_t u_first = c * p.chunk_units - p.head_units;
 
   MrgRegs st;
-  st.a0 = p.x[0]; st.a1 = p.x[1]; st.a2 = p.x[2];
-  st.b0 = p.x[3]; st.b1 = p.x[4]; st.b2 = p.x[5];
-  {
+  if (p.chunk_levels > 0) {
+    // chunk 0 starts at the call's state, chunk c >= 1 at chunk 1's state
+    // jumped by c - 1 chunks; then stream s jumps by s strides
+    const uint32_t* x = c == 0 ? p.x : p.x1;
+    st.a0 = x[0]; st.a1 = x[1]; st.a2 = x[2];
+    st.b0 = x[3]; st.b1 = x[4]; st.b2 = x[5];
+    jump_table(st, p.chunk_tab, p.chunk_levels, active && c > 0 ? (uint64_t)(c - 1) : 0u);
+    if (p.stream_levels > 0) jump_table(st, p.stream_tab, p.stream_levels, active ? (uint64_t)s : 0u);
+  } else {
+    st.a0 = p.x[0]; st.a1 = p.x[1]; st.a2 = p.x[2];
+    st.b0 = p.x[3]; st.b1 = p.x[4]; st.b2 = p.x[5];
     // words to skip: s * stride + max(u_first, 0) * wpu  (mod 2^128)
     uint64_t e_lo = 0, e_hi = 0;
     if (active) {
@@ -153,7 +206,6 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
     jump(st, e_lo, e_hi);
   }
 
-  uint32_t* row = &stage[warp][lane][0];
   const int64_t nsub = p.chunk_units / kSu;
   uint32_t* out_words = reinterpret_cast<uint32_t*>(p.out);
   // Aligned copy-out: lane copies 16-byte piece (lane & 7) of rows
@@ -173,14 +225,25 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
   uint32_t* stream_out = out_words + sw * p.out_words;
   for (int64_t q = 0; q < nsub; ++q) {
     const int64_t ub = u_first + q * kSu;  // first unit of this sub-chunk
+    constexpr int kUpc = 4 / kWpu;          // units per 16-byte chunk
     if (active) {
       if (ub >= 0 && ub + kSu <= p.units) {
 #pragma unroll
-        for (int u = 0; u < kSu; ++u) gen_unit<V>(st, row, u * kWpu, p.t);
+        for (int ch = 0; ch < 8; ++ch) {
+          uint32_t o4[4];
+#pragma unroll
+          for (int u = 0; u < kUpc; ++u) gen_unit<V>(st, o4 + u * kWpu, p.t);
+          stage[warp][lane][ch ^ (lane & 7)] = make_uint4(o4[0], o4[1], o4[2], o4[3]);
+        }
       } else {
-        for (int u = 0; u < kSu; ++u) {
-          const int64_t unit = ub + u;
-          if (unit >= 0 && unit < p.units) gen_unit<V>(st, row, u * kWpu, p.t);
+        for (int ch = 0; ch < 8; ++ch) {
+          uint32_t o4[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+          for (int u = 0; u < kUpc; ++u) {
+            const int64_t unit = ub + ch * kUpc + u;
+            if (unit >= 0 && unit < p.units) gen_unit<V>(st, o4 + u * kWpu, p.t);
+          }
+          stage[warp][lane][ch ^ (lane & 7)] = make_uint4(o4[0], o4[1], o4[2], o4[3]);
         }
       }
     }
@@ -191,10 +254,11 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
         const int r = it * 4 + (lane >> 3);
         if (r >= rows_active) continue;
         const int64_t ow = ow_lane + it * row_stride + q * kRowWords;
-        const uint32_t* src = &stage[warp][r][(lane & 7) * 4];
+        const uint4 v = stage[warp][r][(lane & 7) ^ (r & 7)];
         if (ow >= 0 && ow + 4 <= p.out_words) {
-          store16(stream_out + ow, make_uint4(src[0], src[1], src[2], src[3]));
+          store16(stream_out + ow, v);
         } else {
+          const uint32_t src[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
           for (int i = 0; i < 4; ++i)
             if (ow + i >= 0 && ow + i < p.out_words) stream_out[ow + i] = src[i];
@@ -211,11 +275,60 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
                                        __shfl_sync(0xFFFFFFFFu, ub_lo, r));
         if (!r_active) continue;
         const int64_t ow = r_ub * kWpu + lane;
-        if (ow >= 0 && ow < p.out_words) out_words[r_s * p.out_words + ow] = stage[warp][r][lane];
+        const uint32_t* chunk =
+            reinterpret_cast<const uint32_t*>(&stage[warp][r][(lane >> 2) ^ (r & 7)]);
+        if (ow >= 0 && ow < p.out_words) out_words[r_s * p.out_words + ow] = chunk[lane & 3];
       }
     }
     __syncwarp();
   }
+}
+
+// Host matrix arithmetic for the per-launch tables (3x3 mod m, row-major).
+constexpr mrg::PowTable kHostPow = mrg::make_pow_table();
+
+void host_matmul(const uint32_t* a, const uint32_t* b, uint32_t* out, uint32_t m) {
+  uint32_t r[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      unsigned __int128 acc = 0;
+      for (int k = 0; k < 3; ++k) acc += (unsigned __int128)a[3 * i + k] * b[3 * k + j];
+      r[3 * i + j] = (uint32_t)(acc % m);
+    }
+  std::memcpy(out, r, sizeof(r));
+}
+
+// A_c^e for a 128-bit exponent from the A^(2^j) table.
+void host_pow(int comp, uint64_t e_lo, uint64_t e_hi, uint32_t* out) {
+  const uint32_t m = comp == 0 ? mrg::M1 : mrg::M2;
+  uint32_t r[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  for (int j = 0; j < 128; ++j) {
+    const uint64_t w = j < 64 ? e_lo : e_hi;
+    if ((w >> (j & 63)) & 1u) host_matmul(r, kHostPow.m[comp][j], r, m);
+  }
+  std::memcpy(out, r, sizeof(r));
+}
+
+// tab[k] = A^(e 2^k) for k < levels (both components).
+void host_table(uint64_t e_lo, uint64_t e_hi, int levels, uint32_t (*tab)[2][9]) {
+  for (int c = 0; c < 2; ++c) {
+    const uint32_t m = c == 0 ? mrg::M1 : mrg::M2;
+    uint32_t a[9];
+    host_pow(c, e_lo, e_hi, a);
+    for (int k = 0; k < levels; ++k) {
+      std::memcpy(tab[k][c], a, sizeof(a));
+      host_matmul(a, a, a, m);
+    }
+  }
+}
+
+int bits_for(int64_t v) {  // number of bits to represent v >= 0
+  int b = 0;
+  while (v > 0) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
 }
 
 template <int V>
@@ -260,6 +373,48 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
   p.chunk_units = cu;
   p.chunks_per_stream = cps;
   p.total_chunks = p.chunks_per_stream * r.num_streams;
+  // per-launch jump tables (chunk-granular and stream-granular exponents)
+  const int clev = bits_for(cps - 1), slev = bits_for(r.num_streams - 1);
+  p.chunk_levels = 0;
+  p.stream_levels = 0;
+  if (clev <= kJumpLevels && slev <= kJumpLevels && cps > 1) {
+    static thread_local struct {
+      bool valid = false;
+      uint64_t cw, s_lo, s_hi;
+      int clev, slev;
+      uint32_t ctab[kJumpLevels][2][9], stab[kJumpLevels][2][9];
+    } cache;
+    const uint64_t cw = (uint64_t)cu * I::wpu;
+    if (!(cache.valid && cache.cw == cw && cache.clev >= clev &&
+          (slev == 0 || (cache.s_lo == r.stride_lo && cache.s_hi == r.stride_hi && cache.slev >= slev)))) {
+      host_table(cw, 0, clev, cache.ctab);
+      if (slev > 0) host_table(r.stride_lo, r.stride_hi, slev, cache.stab);
+      cache.valid = true;
+      cache.cw = cw;
+      cache.s_lo = r.stride_lo;
+      cache.s_hi = r.stride_hi;
+      cache.clev = clev;
+      cache.slev = slev;
+    }
+    std::memcpy(p.chunk_tab, cache.ctab, sizeof(p.chunk_tab));
+    std::memcpy(p.stream_tab, cache.stab, sizeof(p.stream_tab));
+    p.chunk_levels = clev;
+    p.stream_levels = slev;
+    // state at the first unit of chunk 1: (cu - head) units after the call's offset
+    uint32_t a[9], b[9];
+    const uint64_t e = (uint64_t)(cu - p.head_units) * I::wpu;
+    host_pow(0, e, 0, a);
+    host_pow(1, e, 0, b);
+    for (int i = 0; i < 3; ++i) {
+      uint64_t acc1 = 0, acc2 = 0;
+      for (int k = 0; k < 3; ++k) {
+        acc1 = (acc1 + (uint64_t)a[3 * i + k] * r.mrg[k] % mrg::M1) % mrg::M1;
+        acc2 = (acc2 + (uint64_t)b[3 * i + k] * r.mrg[3 + k] % mrg::M2) % mrg::M2;
+      }
+      p.x1[i] = (uint32_t)acc1;
+      p.x1[3 + i] = (uint32_t)acc2;
+    }
+  }
   const int64_t grid = (p.total_chunks + kThreads - 1) / kThreads;
   if (grid > 0x7FFFFFFF) {
     set_error("MRG32k3a fill: grid too large");
