@@ -11,14 +11,15 @@
 // -ln u1:  u1 = 2^-e (1 - delta) with e >= 0, delta in (0, 1/2]; a table
 //          factor c_i ~ 1/(1 - i/1024) reduces it to -ln(1 - delta) =
 //          ln c_i - ln(1 - r), 0 <= r < 2^-9, whose series r + r^2/2 + ... +
-//          r^7/7 is summed by Horner.  For i = 0 (u1 within 2^-10 of 1),
+//          r^7/7 is summed by Horner (inner terms in 32-bit fixed point).  For i = 0 (u1 within 2^-10 of 1),
 //          r = delta exactly, so -ln u1 keeps full relative accuracy even
 //          for the smallest delta, 2^-53.
-// rho:     1 / sqrt by two Newton steps from the FP32 reciprocal square root,
-//          then sqrt = x / sqrt(x).
-// sincos:  octant symmetry, a 257-entry table of sin / cos at multiples of
-//          2 pi / 2048 and short Taylor series for the residual angle
-//          phi < 2 pi 2^-11.
+// rho:     1 / sqrt by two Newton steps from the FP32 reciprocal square root
+//          (the first one on the 24-bit seed with narrow products), then
+//          sqrt = x / sqrt(x).
+// sincos:  octant symmetry, a 1025-entry table of sin / cos at multiples of
+//          2 pi / 8192 and two-term series for the residual angle
+//          phi < 2 pi 2^-13.
 // Error: below 2^-55 relative on rho and 2^-60 absolute on sin and cos
 // before the final rounding to double.
 #pragma once
@@ -102,6 +103,10 @@ GRNG_BM_HD void mul64x32(uint64_t a, uint32_t c, uint64_t& hi, uint32_t& lo32) {
   lo32 = (uint32_t)l;
 }
 
+GRNG_BM_HD uint32_t __umulhi32(uint32_t a, uint32_t b) {
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+}
+
 GRNG_BM_HD int clz64(uint64_t x) {  // x != 0
 #if defined(__CUDA_ARCH__)
   return __clzll((long long)x);
@@ -133,14 +138,20 @@ GRNG_BM_HD void neg_log(uint64_t m1, uint64_t& lm, int& le) {
   uint32_t mc_lo;
   mul64x32(M, C, mc_hi, mc_lo);
   const uint64_t R = 0ull - ((mc_hi << 8) | (uint64_t)(mc_lo >> 24));
-  // -ln(1 - r) = r + r^2 (1/2 + r/3 + r^2/4 + r^3/5 + r^4/6 + r^5/7)
-  uint64_t B = kInv7;
-  B = kInv6 + umulhi_apx(R, B);
-  B = kInv5 + umulhi_apx(R, B);
-  B = kInv4 + umulhi_apx(R, B);
-  B = kInv3 + umulhi_apx(R, B);
-  B = kInv2 + umulhi_apx(R, B);
-  const uint64_t S = R + umulhi_apx(umulhi_apx(R, R), B);
+  // -ln(1 - r) = r + r^2 (1/2 + r (1/3 + r B4)), B4 = 1/4 + r/5 + r^2/6 + r^3/7.
+  // r < 2^-9, so r^4 B4 is below 2^-36: B4 in 32-bit fixed point (its error
+  // enters S below 2^-67), the outer two Horner steps in 64-bit.
+  const uint32_t r32 = (uint32_t)(R >> 32);             // r 2^32 < 2^23
+  uint32_t b4 = kInv7_32;
+  b4 = kInv6_32 + __umulhi32(r32, b4);
+  b4 = kInv5_32 + __umulhi32(r32, b4);
+  b4 = kInv4_32 + __umulhi32(r32, b4);
+  uint64_t b4r_hi;                                       // (R b4) >> 32 = r B4 2^64
+  uint32_t b4r_lo;
+  mul64x32(R, b4, b4r_hi, b4r_lo);
+  const uint64_t B3 = kInv3 + b4r_hi;
+  const uint64_t B2 = kInv2 + umulhi_apx(R, B3);
+  const uint64_t S = R + umulhi_apx(umulhi_apx(R, R), B2);
   // L 2^64 = e ln 2 + ln c_i + S, as a 128-bit sum (e ln 2 exactly: 64 x 32)
   uint64_t ln2e_hi;
   uint32_t ln2e_lo;
@@ -177,9 +188,18 @@ GRNG_BM_HD void sqrt2x(uint64_t lm, int le, uint64_t& sq, int& se) {
   uint32_t yb;
   __builtin_memcpy(&yb, &yf, 4);
   const int ey = (int)((yb >> 23) & 0xFFu) - 127;   // 0 or 1
-  uint64_t Y = (uint64_t)((yb & 0x7FFFFFu) | 0x800000u) << (39 + ey);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
+  // first Newton step from the 24-bit seed y0 = m24 2^(ey - 23): its square
+  // and its product with (3 - x y0^2) need only 24 x 32 / 24 x 64 products
+  const uint32_t m24 = (yb & 0x7FFFFFu) | 0x800000u;
+  const uint64_t Y2a = ((uint64_t)m24 * m24) << (14 + 2 * ey);  // y0^2 2^60, exact
+  const uint64_t Tma = (3ull << 60) - umulhi_apx(X, Y2a);        // (3 - x y0^2) 2^60
+  uint64_t t_hi;
+  uint32_t t_lo;
+  mul64x32(Tma, m24, t_hi, t_lo);                   // m24 Tm / 2^32
+  // y1 2^62 = y0 (3 - x y0^2) / 2 2^62 = m24 Tm 2^(ey - 23 - 60 + 61)
+  uint64_t Y = ey >= 0 ? (t_hi << (ey + 10)) | ((uint64_t)t_lo >> (22 - ey))
+                       : (t_hi << 9) | ((uint64_t)t_lo >> 23);
+  {
     const uint64_t Y2 = umulhi_apx(Y, Y);             // y^2 2^60
     const uint64_t XY2 = umulhi_apx(X, Y2);           // x y^2 2^60
     const uint64_t Tm = (3ull << 60) - XY2;           // (3 - x y^2) 2^60
@@ -197,19 +217,17 @@ GRNG_BM_HD void sincos_turns(uint64_t x2, uint64_t& c_abs, bool& c_neg, uint64_t
   const uint32_t o = (uint32_t)(x2 >> 50);          // octant
   uint64_t t = x2 & ((1ull << 50) - 1);
   if (o & 1u) t = (1ull << 50) - t;                 // reflect: angle pi/4 - beta
-  const uint32_t j = (uint32_t)(t >> 42);           // 0..256
-  const uint64_t h = t & ((1ull << 42) - 1);
-  const uint64_t P = umulhi_apx(h << 14, k2Pi61);   // phi 2^64, phi < 2 pi 2^-11
-  const uint64_t P2 = umulhi_apx(P, P);             // phi^2 2^64, < 2^47.3
-  const uint64_t P3 = umulhi_apx(P2, P);            // < 2^39
-  // the small powers only need ~32 significant bits: 32 x 32 products
-  const uint64_t p2s = P2 >> 17;                    // phi^2 2^47, < 2^30.3
-  const uint64_t P4 = (p2s * p2s) >> 30;            // phi^4 2^64, < 2^31
-  const uint64_t P5 = ((P3 >> 8) * p2s) >> 39;      // phi^5 2^64, < 2^23
-  const uint64_t P6 = (P4 * p2s) >> 47;             // phi^6 2^64, < 2^15
-  // sin phi = phi - phi^3/6 + phi^5/120 ; 1 - cos phi = phi^2/2 - phi^4/24 + phi^6/720
-  const uint64_t sphi = P - umulhi_apx(P3, kInv6) + ((P5 * kInv120_32) >> 32);
-  const uint64_t eps = (P2 >> 1) - ((P4 * kInv24_32) >> 32) + ((P6 * kInv720_32) >> 32);
+  const uint32_t j = (uint32_t)(t >> 40);           // 0..1024
+  const uint64_t h = t & ((1ull << 40) - 1);
+  const uint64_t P = umulhi_apx(h << 14, k2Pi61);   // phi 2^64 = 2 pi h 2^11 < 2^53.7
+  const uint64_t P2 = umulhi_apx(P, P);             // phi^2 2^64, < 2^43.3
+  const uint64_t P3 = umulhi_apx(P2, P);            // < 2^33
+  const uint64_t p2s = P2 >> 13;                    // phi^2 2^51, < 2^30.3
+  const uint64_t P4 = (p2s * p2s) >> 38;            // phi^4 2^64, < 2^23
+  // sin phi = phi - phi^3/6 (+ phi^5/120 < 2^-58) ;
+  // 1 - cos phi = phi^2/2 - phi^4/24 (+ phi^6/720 < 2^-71)
+  const uint64_t sphi = P - umulhi_apx(P3, kInv6);
+  const uint64_t eps = (P2 >> 1) - ((P4 * kInv24_32) >> 32);
   const uint64_t Sj = sint(j), Cj = cost(j);
   const uint64_t sn = Sj - umulhi_apx(Sj, eps) + umulhi_apx(Cj, sphi);  // sin(alpha + phi) 2^63
   const uint64_t cs = Cj - umulhi_apx(Cj, eps) - umulhi_apx(Sj, sphi);  // cos(alpha + phi) 2^63

@@ -7,11 +7,12 @@ Tables (emitted as initializer macros GRNG_BM64_LOGC, _LOGT, _SINT, _COST)
   kLogC[i], i = 0..512:  c_i = floor(2^24 / (1 - i/1024)) / 2^24, the reduction
                          factor for -ln(1 - delta) with delta in [i/1024, (i+1)/1024)
   kLogT[i]:              ln(c_i) * 2^64 (c_i exactly as stored)
-  kSinT[j], kCosT[j], j = 0..256:  sin, cos(2 pi j / 2048) * 2^63
+  kSinT[j], kCosT[j], j = 0..1024:  sin, cos(2 pi j / 8192) * 2^63
 Scalars
   kLn2:    ln 2 * 2^64
   k2Pi61:  2 pi * 2^61
   kInv2 .. kInv7: 2^64 / k (truncated)
+  kInv4_32 .. kInv7_32: 2^32 / k (truncated)
   kInv24_32, kInv120_32, kInv720_32: 2^64 / 6 and 2^32 / {24, 120, 720}
 """
 
@@ -41,14 +42,16 @@ def main():
         logt.append(rnd(mp.log(mp.mpf(c) / two24) * two64))
     assert logc[0] == 1 << 24 and logc[512] == 1 << 25
     assert all(t < 1 << 64 for t in logt)
-    sint = [rnd(mp.sin(2 * mp.pi * j / 2048) * two63) for j in range(257)]
-    cost = [rnd(mp.cos(2 * mp.pi * j / 2048) * two63) for j in range(257)]
+    sint = [rnd(mp.sin(2 * mp.pi * j / 8192) * two63) for j in range(1025)]
+    cost = [rnd(mp.cos(2 * mp.pi * j / 8192) * two63) for j in range(1025)]
 
     out.append(f"constexpr uint64_t kLn2 = {rnd(mp.log(2) * two64)}ull;")
     out.append(f"constexpr uint64_t k2Pi61 = {rnd(2 * mp.pi * mp.mpf(2) ** 61)}ull;")
     for k in range(2, 8):
         out.append(f"constexpr uint64_t kInv{k} = {(1 << 64) // k}ull;")
     out.append(f"constexpr uint32_t kInv24_32 = {rnd(mp.mpf(2) ** 32 / 24)}u;")
+    for k in (4, 5, 6, 7):
+        out.append(f"constexpr uint32_t kInv{k}_32 = {(1 << 32) // k}u;")
     out.append(f"constexpr uint32_t kInv120_32 = {rnd(mp.mpf(2) ** 32 / 120)}u;")
     out.append(f"constexpr uint32_t kInv720_32 = {rnd(mp.mpf(2) ** 32 / 720)}u;")
     # table bodies as macros: the device and host copies are declared where used

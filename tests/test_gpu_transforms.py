@@ -3,8 +3,8 @@
 Random engine words almost never reach the edges of the transforms, so here
 the words are built to hit them: u1 = 1 and its neighbours, the smallest u1,
 every power-of-two octave of u1, the boundaries of the log reduction table,
-every octant boundary and table boundary of u2 (FP64 Box-Muller in integer
-fixed point), all 2^24 values of the FP32 uniform, and a sweep of u1 over
+every octant boundary and sincos table boundary of u2 (FP64 Box-Muller in
+integer fixed point), all 2^24 values of the FP32 uniform, and a sweep of u1 over
 its whole FP32 range for the FP32 Box-Muller and lognormal error budgets.
 """
 
@@ -82,9 +82,9 @@ def _fp64_edge_pairs(seed=1, n_random=100000):
             v = o * (1 << 50) + d
             if 0 <= v <= M53:
                 e2.append(v)
-    for j in range(0, 257):
+    for j in range(0, 1025):  # boundaries of the 2 pi / 8192 sincos table
         for d in (-1, 0, 1):
-            v = j * (1 << 42) + d
+            v = j * (1 << 40) + d
             if 0 <= v <= M53:
                 e2.append(v)
     e1 = np.array(sorted(set(e1)), dtype=np.uint64)
