@@ -26,6 +26,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 ENGINE_PHILOX = 0
 ENGINE_MRG = 1
 DIST_BITS, DIST_UNIFORM, DIST_GAUSSIAN, DIST_LOGNORMAL = 0, 1, 2, 3
+DIST_GAUSSIAN_ICDF, DIST_LOGNORMAL_ICDF = 4, 5
 DT_U32, DT_F32, DT_F64 = 0, 1, 2
 
 _lock = threading.Lock()
@@ -175,7 +176,7 @@ def out_dtype(dist: int, dtype: int):
         return np.uint32
     if dist == DIST_UNIFORM:
         return np.float32 if dtype == DT_F32 else np.float64
-    return np.float64  # Box-Muller family: long double result rounded to double
+    return np.float64  # Box-Muller and ICDF families: long double result rounded to double
 
 
 def transform_words(dist: int, dtype: int, p0: float, p1: float, n: int,

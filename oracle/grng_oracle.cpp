@@ -30,6 +30,12 @@
 //         uniform, u2 the [0,1) uniform of the second; z0 = rho cos(2 pi u2),
 //         z1 = rho sin(2 pi u2), rho = sqrt(-2 ln u1); gaussian = mean + sd z,
 //         lognormal = exp(m + s z).  An odd n still consumes the last pair.
+//       - ICDF method (oneMKL's icdf gaussian / lognormal, Sec. 3.1): one
+//         open-interval uniform per output, u = (k + 1/2) 2^-23, k = w >> 9
+//         (FP32) or u = (x + 1/2) 2^-52, x = ((w_a << 32 | w_b) >> 12) (FP64);
+//         z = Phi^-1(u), found by bisection and Newton steps on
+//         Phi(z) = erfc(-z / sqrt 2) / 2 in long double for u <= 1/2 and by
+//         Phi^-1(u) = -Phi^-1(1 - u) above (1 - u is exact).
 //     Gaussian and lognormal values are computed in long double from the
 //     exact u1, u2 and returned rounded to double: this is the FP64 oracle
 //     the tolerances |gpu - oracle| <= 2e-6 max(1,|x|) (FP32) and
@@ -227,7 +233,14 @@ void mrg_skip(MrgState& s, u128 k) {
 
 // ---------------------------------------------------------------- words
 enum { ENGINE_PHILOX = 0, ENGINE_MRG = 1 };
-enum { DIST_BITS = 0, DIST_UNIFORM = 1, DIST_GAUSSIAN = 2, DIST_LOGNORMAL = 3 };
+enum {
+  DIST_BITS = 0,
+  DIST_UNIFORM = 1,
+  DIST_GAUSSIAN = 2,
+  DIST_LOGNORMAL = 3,
+  DIST_GAUSSIAN_ICDF = 4,
+  DIST_LOGNORMAL_ICDF = 5
+};
 enum { DT_U32 = 0, DT_F32 = 1, DT_F64 = 2 };
 
 u128 make_u128(uint64_t lo, uint64_t hi) { return ((u128)hi << 64) | (u128)lo; }
@@ -285,6 +298,49 @@ void box_muller_ld(long double u1, long double u2, long double* z0, long double*
   *z1 = rho * std::sin(ang);
 }
 
+// ---------------------------------------------------------------- ICDF
+// Inverse-CDF method (oneMKL's icdf method of its gaussian / lognormal
+// distributions, Sec. 3.1): z = Phi^-1(u) for one open-interval uniform per
+// output.  Reading: u = (k + 1/2) 2^-23 with k = w >> 9 (FP32) and
+// u = (x + 1/2) 2^-52 with x = ((w_a << 32 | w_b) >> 12) (FP64), exact
+// midpoints in (0, 1) symmetric about 1/2.
+float u_mid_f32(uint32_t w) { return (float)std::ldexp(2.0 * (double)(w >> 9) + 1.0, -24); }
+double u_mid_f64(uint32_t wa, uint32_t wb) {
+  uint64_t x = (((uint64_t)wa << 32) | (uint64_t)wb) >> 12;
+  return std::ldexp(2.0 * (double)x + 1.0, -53);
+}
+
+// Phi(z) = erfc(-z / sqrt 2) / 2 in long double.
+long double phi_ld(long double z) {
+  const long double SQRT1_2 = 0.707106781186547524400844362104849039L;
+  return 0.5L * std::erfc(-z * SQRT1_2);
+}
+
+// Phi^-1(u) by bisection on Phi (monotone), then Newton steps; plain and slow.
+// Only called for u <= 1/2, where Phi(z) = erfc(-z / sqrt 2) / 2 keeps full
+// relative precision; the upper half uses Phi^-1(u) = -Phi^-1(1 - u) with
+// 1 - u exact (see icdf_z).
+long double inv_phi_lower(long double u) {
+  long double lo = -40.0L, hi = 40.0L;
+  for (int it = 0; it < 200; ++it) {  // bisection to a tight bracket
+    long double mid = 0.5L * (lo + hi);
+    if (phi_ld(mid) < u) lo = mid; else hi = mid;
+    if (hi - lo < 1e-12L) break;
+  }
+  long double z = 0.5L * (lo + hi);
+  const long double INV_SQRT_2PI = 0.398942280401432677939946059934381868L;
+  for (int it = 0; it < 4; ++it) {  // Newton: z -= (Phi(z) - u) / phi(z)
+    long double dens = INV_SQRT_2PI * std::exp(-0.5L * z * z);
+    z -= (phi_ld(z) - u) / dens;
+  }
+  return z;
+}
+
+// z = Phi^-1(u) for an exact midpoint u in (0, 1).
+long double icdf_z(long double u) {
+  return u <= 0.5L ? inv_phi_lower(u) : -inv_phi_lower(1.0L - u);
+}
+
 int words_per_output(int dtype) { return dtype == DT_F64 ? 2 : 1; }
 
 bool is_pair_dist(int dist) { return dist == DIST_GAUSSIAN || dist == DIST_LOGNORMAL; }
@@ -299,7 +355,8 @@ uint64_t words_for(int dist, int dtype, int64_t n) {
 
 bool valid_combo(int dist, int dtype) {
   if (dist == DIST_BITS) return dtype == DT_U32;
-  if (dist == DIST_UNIFORM || dist == DIST_GAUSSIAN || dist == DIST_LOGNORMAL)
+  if (dist == DIST_UNIFORM || dist == DIST_GAUSSIAN || dist == DIST_LOGNORMAL ||
+      dist == DIST_GAUSSIAN_ICDF || dist == DIST_LOGNORMAL_ICDF)
     return dtype == DT_F32 || dtype == DT_F64;
   return false;
 }
@@ -323,6 +380,25 @@ void transform_words(int dist, int dtype, double p0, double p1, int64_t n,
     } else {
       double* o = (double*)out;
       for (int64_t i = 0; i < n; ++i) o[i] = range_f64(u01_f64(w[2 * i], w[2 * i + 1]), p0, p1);
+    }
+    return;
+  }
+  if (dist == DIST_GAUSSIAN_ICDF || dist == DIST_LOGNORMAL_ICDF) {
+    double* o = (double*)out;
+    long double mean, sd;
+    if (dtype == DT_F32) {
+      mean = (long double)(float)p0;
+      sd = (long double)(float)p1;
+    } else {
+      mean = (long double)p0;
+      sd = (long double)p1;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      long double u = dtype == DT_F32 ? (long double)u_mid_f32(w[i])
+                                      : (long double)u_mid_f64(w[2 * i], w[2 * i + 1]);
+      long double v = mean + sd * icdf_z(u);
+      if (dist == DIST_LOGNORMAL_ICDF) v = std::exp(v);
+      o[i] = (double)v;
     }
     return;
   }
