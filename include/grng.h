@@ -38,7 +38,8 @@
  * Words per output (the consumption rule; the paper does not fix one):
  *   bits U32: 1 | uniform F32: 1 | uniform F64: 2 (the earlier word is the
  *   high half) | gaussian / lognormal F32: 1, F64: 2, consumed in
- *   Box-Muller pairs: an odd n still consumes its last pair whole.
+ *   Box-Muller pairs: an odd n still consumes its last pair whole |
+ *   ICDF gaussian / lognormal F32: 1, F64: 2 (no pairing).
  */
 #ifndef GRNG_H
 #define GRNG_H
@@ -75,7 +76,9 @@ typedef enum grng_dist_kind {
   GRNG_BITS = 0,      /* raw 32-bit words; dtype must be GRNG_U32 */
   GRNG_UNIFORM = 1,   /* [p0, p1) = [a, b) */
   GRNG_GAUSSIAN = 2,  /* Box-Muller; p0 = mean, p1 = stddev > 0 */
-  GRNG_LOGNORMAL = 3  /* exp(m + s z), z Box-Muller; p0 = m, p1 = s > 0 */
+  GRNG_LOGNORMAL = 3, /* exp(m + s z), z Box-Muller; p0 = m, p1 = s > 0 */
+  GRNG_GAUSSIAN_ICDF = 4,  /* inverse-CDF method; p0 = mean, p1 = stddev > 0 */
+  GRNG_LOGNORMAL_ICDF = 5  /* exp(m + s z), z by the inverse-CDF method */
 } grng_dist_kind;
 
 typedef enum grng_dtype { GRNG_U32 = 0, GRNG_F32 = 1, GRNG_F64 = 2 } grng_dtype;
@@ -93,6 +96,11 @@ typedef enum grng_dtype { GRNG_U32 = 0, GRNG_F32 = 1, GRNG_F64 = 2 } grng_dtype;
  *             second; z0 = rho cos(2 pi u2), z1 = rho sin(2 pi u2),
  *             rho = sqrt(-2 ln u1); output mean + stddev z.
  *   lognormal: exp(m + s z) with z as for gaussian.
+ *   gaussian / lognormal ICDF (oneMKL's icdf method, which cuRAND offers
+ *             only for quasi-random generators, Sec. 3.1): one uniform per
+ *             output, u = (k + 1/2) 2^-23 with k = w >> 9 (F32) or
+ *             u = (x + 1/2) 2^-52 with x = ((w_a << 32 | w_b) >> 12) (F64),
+ *             z = Phi^-1(u) (CUDA's normcdfinvf / normcdfinv).
  * Uniform and bits outputs are bit-exact functions of the words; gaussian and
  * lognormal outputs are within 2e-6 max(1, |x|) (F32) or 1e-14 max(1, |x|)
  * (F64) of the exact value.

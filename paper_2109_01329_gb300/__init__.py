@@ -5,13 +5,13 @@ gaussian, lognormal) behind the C ABI of include/grng.h, implemented by
 hand-written CUDA kernels in csrc/.  This package is the thin Python binding.
 """
 
-from ._binding import (BITS, Batch, Server, serve_request, F32, F64, GAUSSIAN, LOGNORMAL, MRG32K3A, PHILOX4X32X10, U32,
+from ._binding import (BITS, GAUSSIAN_ICDF, LOGNORMAL_ICDF, Batch, Server, serve_request, F32, F64, GAUSSIAN, LOGNORMAL, MRG32K3A, PHILOX4X32X10, U32,
                        UNIFORM, Distribution, Engine, GrngError, generate, generate_host,
                        generate_host_static,
                        generate_ptr, generate_substreams, load, transform_words, words_for)
 from ._binding import LIB_PATH, EXPORTED
 
-__all__ = ["BITS", "Batch", "Server", "serve_request", "F32", "F64", "GAUSSIAN", "LOGNORMAL", "MRG32K3A", "PHILOX4X32X10", "U32",
+__all__ = ["BITS", "GAUSSIAN_ICDF", "LOGNORMAL_ICDF", "Batch", "Server", "serve_request", "F32", "F64", "GAUSSIAN", "LOGNORMAL", "MRG32K3A", "PHILOX4X32X10", "U32",
            "UNIFORM", "Distribution", "Engine", "GrngError", "generate", "generate_host",
            "generate_host_static",
            "generate_ptr", "generate_substreams", "load", "transform_words", "words_for", "LIB_PATH", "EXPORTED"]

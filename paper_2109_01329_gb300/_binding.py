@@ -22,6 +22,7 @@ ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET = 1
 PHILOX4X32X10 = 0
 MRG32K3A = 1
 BITS, UNIFORM, GAUSSIAN, LOGNORMAL = 0, 1, 2, 3
+GAUSSIAN_ICDF, LOGNORMAL_ICDF = 4, 5
 U32, F32, F64 = 0, 1, 2
 
 EXPORTED = ["grng_status_string", "grng_last_error", "grng_engine_create", "grng_engine_restore",
@@ -191,6 +192,14 @@ class Distribution:
     @staticmethod
     def lognormal(m: float = 0.0, s: float = 1.0, dtype: int = F32) -> "Distribution":
         return Distribution(LOGNORMAL, dtype, m, s)
+
+    @staticmethod
+    def gaussian_icdf(mean: float = 0.0, stddev: float = 1.0, dtype: int = F32) -> "Distribution":
+        return Distribution(GAUSSIAN_ICDF, dtype, mean, stddev)
+
+    @staticmethod
+    def lognormal_icdf(m: float = 0.0, s: float = 1.0, dtype: int = F32) -> "Distribution":
+        return Distribution(LOGNORMAL_ICDF, dtype, m, s)
 
 
 class Engine:

@@ -122,7 +122,9 @@ grng_status check_dist(const grng_distribution* d) {
       return GRNG_OK;
     }
     case GRNG_GAUSSIAN:
-    case GRNG_LOGNORMAL: {
+    case GRNG_LOGNORMAL:
+    case GRNG_GAUSSIAN_ICDF:
+    case GRNG_LOGNORMAL_ICDF: {
       if (!dt_float) {
         set_error("gaussian / lognormal need dtype F32 or F64");
         return GRNG_ERR_INVALID_ARG;
@@ -214,6 +216,18 @@ int choose_variant(const grng_distribution* d, TransformParams* t) {
       t->dsd = d->p1;
       t->std_normal = (d->p0 == 0.0 && d->p1 == 1.0) ? 1 : 0;
       return logn ? V_LOGN_F64 : V_GAUSS_F64;
+    }
+    case GRNG_GAUSSIAN_ICDF:
+    case GRNG_LOGNORMAL_ICDF: {
+      const bool logn = d->kind == GRNG_LOGNORMAL_ICDF;
+      if (d->dtype == GRNG_F32) {
+        t->fmean = (float)d->p0;
+        t->fsd = (float)d->p1;
+        return logn ? V_ICDF_LOGN_F32 : V_ICDF_GAUSS_F32;
+      }
+      t->dmean = d->p0;
+      t->dsd = d->p1;
+      return logn ? V_ICDF_LOGN_F64 : V_ICDF_GAUSS_F64;
     }
     default: return -1;
   }

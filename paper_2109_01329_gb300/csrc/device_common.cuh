@@ -154,6 +154,21 @@ __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
     }
     o[0] = __float_as_uint(y0);
     o[1] = __float_as_uint(y1);
+  } else if constexpr (V == V_ICDF_GAUSS_F32 || V == V_ICDF_LOGN_F32) {
+    // u = (k + 1/2) 2^-23, k = w >> 9: an exact midpoint in (0, 1)
+    const float u = __uint2float_rn(2u * (w[0] >> 9) + 1u) * 0x1p-24f;
+    float y = fmaf(t.fsd, normcdfinvf(u), t.fmean);
+    if constexpr (V == V_ICDF_LOGN_F32) y = expf(y);
+    o[0] = __float_as_uint(y);
+  } else if constexpr (V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64) {
+    // u = (x + 1/2) 2^-52, x = ((w_a << 32) | w_b) >> 12
+    const uint64_t x = ((((uint64_t)w[0]) << 32) | (uint64_t)w[1]) >> 12;
+    const double u = scaled_u54_to_f64(2u * x + 1u, -53);
+    double y = fma(t.dsd, normcdfinv(u), t.dmean);
+    if constexpr (V == V_ICDF_LOGN_F64) y = exp(y);
+    const uint64_t b = (uint64_t)__double_as_longlong(y);
+    o[0] = (uint32_t)b;
+    o[1] = (uint32_t)(b >> 32);
   } else {  // V_GAUSS_F64, V_LOGN_F64
     double z0, z1;
     box_muller_f64(w[0], w[1], w[2], w[3], z0, z1);
@@ -179,9 +194,11 @@ __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
 // 4 / wpu whole units (the aligned case).
 template <int V>
 __device__ __forceinline__ uint4 block_outputs(uint4 b, const TransformParams& t) {
-  constexpr int kWpu = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 1
-                       : (V == V_GAUSS_F64 || V == V_LOGN_F64)          ? 4
-                                                                         : 2;
+  constexpr int kWpu = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32 ||
+                        V == V_ICDF_GAUSS_F32 || V == V_ICDF_LOGN_F32)
+                           ? 1
+                       : (V == V_GAUSS_F64 || V == V_LOGN_F64) ? 4
+                                                                 : 2;
   uint32_t w[4] = {b.x, b.y, b.z, b.w};
   uint32_t o[4];
 #pragma unroll
@@ -191,11 +208,14 @@ __device__ __forceinline__ uint4 block_outputs(uint4 b, const TransformParams& t
 
 template <int V>
 struct VInfo {
-  static constexpr int wpu = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 1
-                             : (V == V_GAUSS_F64 || V == V_LOGN_F64)          ? 4
-                                                                               : 2;
+  static constexpr int wpu = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32 ||
+                              V == V_ICDF_GAUSS_F32 || V == V_ICDF_LOGN_F32)
+                                 ? 1
+                             : (V == V_GAUSS_F64 || V == V_LOGN_F64) ? 4
+                                                                       : 2;
   static constexpr int es = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32 ||
-                             V == V_GAUSS_F32 || V == V_LOGN_F32)
+                             V == V_GAUSS_F32 || V == V_LOGN_F32 || V == V_ICDF_GAUSS_F32 ||
+                             V == V_ICDF_LOGN_F32)
                                 ? 4
                                 : 8;
   static constexpr int epu = (V == V_GAUSS_F32 || V == V_LOGN_F32 || V == V_GAUSS_F64 ||

@@ -23,7 +23,11 @@ enum Variant : int {
   V_LOGN_F32 = 7,
   V_GAUSS_F64 = 8,
   V_LOGN_F64 = 9,
-  V_COUNT = 10
+  V_ICDF_GAUSS_F32 = 10,  // inverse-CDF gaussian / lognormal: one uniform per output
+  V_ICDF_LOGN_F32 = 11,
+  V_ICDF_GAUSS_F64 = 12,
+  V_ICDF_LOGN_F64 = 13,
+  V_COUNT = 14
 };
 
 // Geometry of a variant.  Every variant produces 4 output bytes per word it
@@ -39,6 +43,8 @@ inline VariantInfo variant_info(int v) {
     case V_BITS: case V_U01_F32: case V_UNI_F32: return {4, 1, 1};
     case V_U01_F64: case V_AFF_F64: case V_UNI_F64: return {8, 2, 1};
     case V_GAUSS_F32: case V_LOGN_F32: return {4, 2, 2};
+    case V_ICDF_GAUSS_F32: case V_ICDF_LOGN_F32: return {4, 1, 1};
+    case V_ICDF_GAUSS_F64: case V_ICDF_LOGN_F64: return {8, 2, 1};
     default: return {8, 4, 2};  // V_GAUSS_F64, V_LOGN_F64
   }
 }

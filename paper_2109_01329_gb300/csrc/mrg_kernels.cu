@@ -447,6 +447,10 @@ grng_status launch_mrg(const FillRequest& r, CUstream_st* stream) {
     case V_LOGN_F32: return launch_variant<V_LOGN_F32>(r, stream);
     case V_GAUSS_F64: return launch_variant<V_GAUSS_F64>(r, stream);
     case V_LOGN_F64: return launch_variant<V_LOGN_F64>(r, stream);
+    case V_ICDF_GAUSS_F32: return launch_variant<V_ICDF_GAUSS_F32>(r, stream);
+    case V_ICDF_LOGN_F32: return launch_variant<V_ICDF_LOGN_F32>(r, stream);
+    case V_ICDF_GAUSS_F64: return launch_variant<V_ICDF_GAUSS_F64>(r, stream);
+    case V_ICDF_LOGN_F64: return launch_variant<V_ICDF_LOGN_F64>(r, stream);
     default: set_error("unknown variant %d", r.variant); return GRNG_ERR_INVALID_ARG;
   }
 }

@@ -49,7 +49,7 @@ def _host(t):
 
 VARS = [(0, 0, 0.0, 0.0), (1, 1, 0.0, 1.0), (1, 1, -2.5, 7.0), (1, 2, 0.0, 1.0),
         (1, 2, -1.0, 1.0), (1, 2, 2.0, 5.0), (2, 1, 0.5, 2.0), (3, 1, 0.0, 1.0),
-        (2, 2, 0.0, 1.0), (3, 2, 0.25, 0.5)]
+        (2, 2, 0.0, 1.0), (3, 2, 0.25, 0.5), (4, 1, 0.0, 1.0), (5, 2, 0.0, 0.5)]
 
 
 def _mixed_requests(g, seed=3, count=60):

@@ -32,6 +32,10 @@ VARIANTS = [
     ("logn_f32", 3, 1, 0.0, 1.0),
     ("gauss_f64", 2, 2, -1.0, 0.5),
     ("logn_f64", 3, 2, 0.25, 0.75),
+    ("icdf_gauss_f32", 4, 1, 0.5, 2.0),
+    ("icdf_logn_f32", 5, 1, 0.0, 1.0),
+    ("icdf_gauss_f64", 4, 2, 0.0, 1.0),
+    ("icdf_logn_f64", 5, 2, 0.25, 0.5),
 ]
 
 SENTINEL = 0xA5

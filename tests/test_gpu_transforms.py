@@ -160,3 +160,31 @@ def test_transform_odd_n_and_random(g, var):
         got = _gpu(g, kind, dtype, p0, p1, w, n)
         ref = oracle.transform_words(kind, dtype, p0, p1, n, w)
         _check(kind, dtype, got, ref, f"{var} n={n}")
+
+
+@pytest.mark.parametrize("kind,p0,p1", [(4, 0.0, 1.0), (5, 0.0, 1.0), (4, -1.0, 3.0)])
+def test_icdf_f32_tails_and_sweep(g, kind, p0, p1):
+    """Every k in both tails (k < 4096 and k > 2^23 - 4096) and every 61st k
+    in between: the inverse CDF meets the FP32 tolerance across (0, 1)."""
+    k = np.concatenate([np.arange(0, 4096), np.arange((1 << 23) - 4096, 1 << 23),
+                        np.arange(4096, (1 << 23) - 4096, 61)]).astype(np.uint32)
+    w = (k << np.uint32(9)) | np.uint32(0x155)
+    got = _gpu(g, kind, 1, p0, p1, w, w.size)
+    ref = oracle.transform_words(kind, 1, p0, p1, w.size, w)
+    worst = _check(kind, 1, got, ref, f"ICDF FP32 kind {kind}")
+    print(f"ICDF FP32 kind {kind}: worst error / max(1,|x|) = {worst:.3e}")
+
+
+@pytest.mark.parametrize("kind", [4, 5])
+def test_icdf_f64_tails(g, kind):
+    rng = np.random.Generator(np.random.PCG64(8))
+    x = np.concatenate([np.arange(0, 2048, dtype=np.uint64),
+                        (1 << 52) - 1 - np.arange(0, 2048, dtype=np.uint64),
+                        rng.integers(0, 1 << 52, 20000, dtype=np.uint64)])
+    x = x << np.uint64(12)  # the 52-bit integer of the FP64 ICDF uniform
+    wa = (x >> np.uint64(32)).astype(np.uint32)
+    wb = (x & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    w = np.stack([wa, wb], axis=1).reshape(-1)
+    got = _gpu(g, kind, 2, 0.0, 1.0, w, wa.size)
+    ref = oracle.transform_words(kind, 2, 0.0, 1.0, wa.size, w)
+    _check(kind, 2, got, ref, f"ICDF FP64 kind {kind}")
