@@ -115,10 +115,11 @@ typedef struct grng_distribution {
 /* Serialisable engine state (checkpoint / resume). */
 typedef struct grng_engine_state {
   int32_t kind;        /* grng_engine_kind */
-  uint32_t reserved;   /* zero */
-  uint64_t seed;
+  uint32_t reserved;   /* number of MRG32k3a seed words in words[] (0: seeded by seed) */
+  uint64_t seed;       /* the seed, or the Philox key of a word-seeded Philox engine */
   uint64_t offset_lo;  /* 128-bit word offset = offset_lo + 2^64 offset_hi */
   uint64_t offset_hi;
+  uint32_t words[6];   /* MRG32k3a seed words (see grng_engine_create_words) */
 } grng_engine_state;
 
 typedef struct grng_engine* grng_engine_t;
@@ -138,6 +139,20 @@ GRNG_API const char* grng_last_error(void);
  * Errors: INVALID_ARG (out NULL, bad kind), OOM.
  */
 GRNG_API grng_status grng_engine_create(grng_engine_t* out, int32_t kind, uint64_t seed, uint64_t offset);
+
+/*
+ * Creates an engine from a seed initializer list of `count` (1..6) 32-bit
+ * words (oneMKL engines accept such lists; cuRAND's do not, Sec. 3.1):
+ *   Philox4x32-10: words 0, 1 = key (k0, k1); words 2..5 = the starting
+ *     128-bit block counter (c0..c3; missing words 0), i.e. word offset
+ *     4 * counter (mod 2^128) + offset.  {lo, hi} equals seed lo + 2^32 hi.
+ *   MRG32k3a: words 0..2 = x1_{-1}, x1_{-2}, x1_{-3} (mod m1) and words 3..5 =
+ *     x2_{-1}, x2_{-2}, x2_{-3} (mod m2); missing words are 1, so {w} equals
+ *     the single seed w.  A component state of all zeros is INVALID_ARG.
+ */
+GRNG_API grng_status grng_engine_create_words(grng_engine_t* out, int32_t kind,
+                                              const uint32_t* words, int32_t count,
+                                              uint64_t offset);
 
 /* Creates an engine from a saved state (checkpoint / resume). */
 GRNG_API grng_status grng_engine_restore(grng_engine_t* out, const grng_engine_state* state);

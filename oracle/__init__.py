@@ -85,6 +85,11 @@ def lib() -> ctypes.CDLL:
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                           ctypes.c_void_p]
             L.oracle_generate.restype = ctypes.c_int
+            L.oracle_generate_words.argtypes = [ctypes.c_int, u32p, ctypes.c_int, ctypes.c_uint64,
+                                                ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                                ctypes.c_void_p]
+            L.oracle_generate_words.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -201,4 +206,17 @@ def generate(engine: int, seed: int, offset: int, dist: int, dtype: int, p0: flo
                                out.ctypes.data)
     if rc != 0:
         raise ValueError("oracle_generate: invalid argument")
+    return out
+
+
+def generate_words(engine: int, words, offset: int, dist: int, dtype: int, p0: float, p1: float,
+                   n: int) -> np.ndarray:
+    """As generate, for an engine seeded by a list of 1..6 32-bit words."""
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint64).astype(np.uint32))
+    out = np.empty(max(n, 0), dtype=out_dtype(dist, dtype))
+    lo, hi = _split128(offset)
+    rc = lib().oracle_generate_words(engine, _u32p(w), int(w.size), lo, hi, dist, dtype, p0, p1,
+                                     n, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_generate_words: invalid argument")
     return out

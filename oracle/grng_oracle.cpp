@@ -533,4 +533,41 @@ int oracle_generate(int engine, uint64_t seed, uint64_t off_lo, uint64_t off_hi,
   return 0;
 }
 
+// The whole path for an engine seeded by a list of 1..6 32-bit words
+// (oneMKL's seed initializer lists, Sec. 3.1).  Reading: Philox key = words
+// 0, 1 and starting block counter = words 2..5 (word offset 4 counter + off);
+// MRG32k3a x1_{-1}, x1_{-2}, x1_{-3} = words 0..2 (mod m1) and x2_{-1},
+// x2_{-2}, x2_{-3} = words 3..5 (mod m2), missing words 1.
+int oracle_generate_words(int engine, const uint32_t* words, int count, uint64_t off_lo,
+                          uint64_t off_hi, int dist, int dtype, double p0, double p1, int64_t n,
+                          void* out) {
+  if (n < 0 || count < 1 || count > 6 || !valid_combo(dist, dtype)) return 1;
+  uint32_t w[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < count; ++i) w[i] = words[i];
+  const u128 off = make_u128(off_lo, off_hi);
+  const uint64_t nw = words_for(dist, dtype, n);
+  uint32_t* buf = new uint32_t[nw > 0 ? nw : 1];
+  if (engine == ENGINE_PHILOX) {
+    const uint64_t seed = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+    u128 counter = 0;
+    for (int i = 0; i < 4; ++i) counter |= (u128)w[2 + i] << (32 * i);
+    const u128 start = counter * 4 + off;
+    for (uint64_t i = 0; i < nw; ++i) buf[i] = philox_word(seed, start + (u128)i);
+  } else if (engine == ENGINE_MRG) {
+    MrgState st;
+    for (int i = 0; i < 3; ++i) {
+      st.x1[2 - i] = i < count ? (int64_t)(w[i] % (uint32_t)MRG_M1) : 1;
+      st.x2[2 - i] = 3 + i < count ? (int64_t)(w[3 + i] % (uint32_t)MRG_M2) : 1;
+    }
+    mrg_skip(st, off);
+    for (uint64_t i = 0; i < nw; ++i) buf[i] = mrg_step(st);
+  } else {
+    delete[] buf;
+    return 1;
+  }
+  transform_words(dist, dtype, p0, p1, n, buf, out);
+  delete[] buf;
+  return 0;
+}
+
 }  // extern "C"

@@ -25,7 +25,8 @@ BITS, UNIFORM, GAUSSIAN, LOGNORMAL = 0, 1, 2, 3
 GAUSSIAN_ICDF, LOGNORMAL_ICDF = 4, 5
 U32, F32, F64 = 0, 1, 2
 
-EXPORTED = ["grng_status_string", "grng_last_error", "grng_engine_create", "grng_engine_restore",
+EXPORTED = ["grng_status_string", "grng_last_error", "grng_engine_create",
+            "grng_engine_create_words", "grng_engine_restore",
             "grng_engine_copy", "grng_engine_skip_ahead", "grng_engine_get_state",
             "grng_engine_destroy", "grng_words_for", "grng_generate",
             "grng_generate_substreams", "grng_generate_host", "grng_generate_host_static",
@@ -51,7 +52,7 @@ class _Dist(ctypes.Structure):
 class _State(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("offset_lo", ctypes.c_uint64),
-                ("offset_hi", ctypes.c_uint64)]
+                ("offset_hi", ctypes.c_uint64), ("words", ctypes.c_uint32 * 6)]
 
 
 class _Request(ctypes.Structure):
@@ -102,6 +103,9 @@ def load() -> ctypes.CDLL:
         L.grng_engine_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_uint64,
                                          ctypes.c_uint64]
         L.grng_engine_restore.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_State)]
+        L.grng_engine_create_words.argtypes = [ctypes.POINTER(vp), ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32,
+                                               ctypes.c_uint64]
         L.grng_engine_copy.argtypes = [ctypes.POINTER(vp), vp]
         L.grng_engine_skip_ahead.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64]
         L.grng_engine_get_state.argtypes = [vp, ctypes.POINTER(_State)]
@@ -218,10 +222,34 @@ class Engine:
                 _check(L.grng_engine_skip_ahead(self._h, 0, hi), "grng_engine_skip_ahead")
 
     @classmethod
-    def restore(cls, state: tuple) -> "Engine":
-        kind, seed, offset = state
+    def from_words(cls, kind: int, words, offset: int = 0) -> "Engine":
+        """An engine from a seed initializer list of 1..6 32-bit words."""
+        arr = (ctypes.c_uint32 * len(words))(*[int(w) & 0xFFFFFFFF for w in words])
+        h = ctypes.c_void_p()
+        _check(load().grng_engine_create_words(ctypes.byref(h), kind, arr, len(words),
+                                               offset % (1 << 64)), "grng_engine_create_words")
+        return cls(kind, 0, _handle=h)
+
+    @property
+    def full_state(self) -> dict:
+        st = _State()
+        _check(load().grng_engine_get_state(self._h, ctypes.byref(st)), "grng_engine_get_state")
+        return {"kind": st.kind, "seed": st.seed, "offset": st.offset_lo | (st.offset_hi << 64),
+                "words": list(st.words)[: st.reserved]}
+
+    @classmethod
+    def restore(cls, state) -> "Engine":
+        """From (kind, seed, offset) or a full_state dict."""
+        if isinstance(state, dict):
+            kind, seed, offset = state["kind"], state["seed"], state["offset"]
+            words = state.get("words", [])
+        else:
+            kind, seed, offset = state
+            words = []
         lo, hi = _split128(offset)
-        st = _State(kind, 0, seed % (1 << 64), lo, hi)
+        st = _State(kind, len(words), seed % (1 << 64), lo, hi)
+        for i, w in enumerate(words):
+            st.words[i] = int(w) & 0xFFFFFFFF
         h = ctypes.c_void_p()
         _check(load().grng_engine_restore(ctypes.byref(h), ctypes.byref(st)),
                "grng_engine_restore")

@@ -20,7 +20,9 @@
 
 struct grng_engine {
   int32_t kind;
-  uint64_t seed;
+  uint64_t seed;            // single seed, or the Philox key of a word seed
+  uint32_t nwords;          // 0: seeded by `seed`; 1..6: by words[]
+  uint32_t words[6];
   uint64_t off_lo, off_hi;  // 128-bit word offset
   uint32_t mrg[6];          // MRG32k3a: state at the current offset
 };
@@ -52,6 +54,16 @@ void mrg_seed_state(uint64_t seed, uint32_t* st) {
   st[5] = 1;
 }
 
+// MRG32k3a state from seed words: words 0..2 are x1_{-1}, x1_{-2}, x1_{-3}
+// (mod m1), words 3..5 the same for x2 (mod m2); missing words are 1, so one
+// word w gives the single-seed state (1, 1, w mod m1), (1, 1, 1).
+void mrg_words_state(const uint32_t* w, uint32_t n, uint32_t* st) {
+  for (int i = 0; i < 3; ++i) {
+    st[2 - i] = i < (int)n ? w[i] % mrg::M1 : 1u;
+    st[5 - i] = 3 + i < (int)n ? w[3 + i] % mrg::M2 : 1u;
+  }
+}
+
 void init_engine(grng_engine* e, int32_t kind, uint64_t seed, uint64_t off_lo, uint64_t off_hi) {
   e->kind = kind;
   e->seed = seed;
@@ -59,7 +71,11 @@ void init_engine(grng_engine* e, int32_t kind, uint64_t seed, uint64_t off_lo, u
   e->off_hi = off_hi;
   std::memset(e->mrg, 0, sizeof(e->mrg));
   if (kind == GRNG_MRG32K3A) {
-    mrg_seed_state(seed, e->mrg);
+    if (e->nwords > 0) {
+      mrg_words_state(e->words, e->nwords, e->mrg);
+    } else {
+      mrg_seed_state(seed, e->mrg);
+    }
     mrg_jump_host(e->mrg, off_lo, off_hi);
   }
 }
@@ -336,6 +352,47 @@ const char* grng_status_string(grng_status s) {
 
 const char* grng_last_error(void) { return g_last_error; }
 
+grng_status grng_engine_create_words(grng_engine_t* out, int32_t kind, const uint32_t* words,
+                                     int32_t count, uint64_t offset) {
+  if (out == nullptr || (count > 0 && words == nullptr) || count < 1 || count > 6) {
+    set_error("out NULL, words NULL or count not in [1, 6]");
+    return GRNG_ERR_INVALID_ARG;
+  }
+  if (kind != GRNG_PHILOX4X32X10 && kind != GRNG_MRG32K3A) {
+    set_error("unknown engine kind %d", kind);
+    return GRNG_ERR_INVALID_ARG;
+  }
+  uint32_t w[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < count; ++i) w[i] = words[i];
+  uint64_t seed = 0, off_lo = offset, off_hi = 0;
+  if (kind == GRNG_PHILOX4X32X10) {
+    // key = words 0, 1; counter = words 2..5; word offset = 4 counter + offset
+    seed = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+    const uint64_t c_lo = (uint64_t)w[2] | ((uint64_t)w[3] << 32);
+    const uint64_t c_hi = (uint64_t)w[4] | ((uint64_t)w[5] << 32);
+    const uint64_t b_lo = c_lo << 2, b_hi = (c_hi << 2) | (c_lo >> 62);
+    off_lo = b_lo + offset;
+    off_hi = b_hi + ((off_lo < b_lo) ? 1u : 0u);
+  } else {
+    uint32_t st[6];
+    mrg_words_state(w, (uint32_t)count, st);
+    if ((st[0] | st[1] | st[2]) == 0 || (st[3] | st[4] | st[5]) == 0) {
+      set_error("an MRG32k3a component state of all zeros never leaves zero");
+      return GRNG_ERR_INVALID_ARG;
+    }
+  }
+  grng_engine* e = new (std::nothrow) grng_engine;
+  if (e == nullptr) {
+    set_error("engine allocation failed");
+    return GRNG_ERR_OOM;
+  }
+  e->nwords = kind == GRNG_MRG32K3A ? (uint32_t)count : 0u;
+  std::memcpy(e->words, w, sizeof(w));
+  init_engine(e, kind, seed, off_lo, off_hi);
+  *out = e;
+  return GRNG_OK;
+}
+
 grng_status grng_engine_create(grng_engine_t* out, int32_t kind, uint64_t seed, uint64_t offset) {
   if (out == nullptr) {
     set_error("out is NULL");
@@ -350,6 +407,8 @@ grng_status grng_engine_create(grng_engine_t* out, int32_t kind, uint64_t seed, 
     set_error("engine allocation failed");
     return GRNG_ERR_OOM;
   }
+  e->nwords = 0;
+  std::memset(e->words, 0, sizeof(e->words));
   init_engine(e, kind, seed, offset, 0);
   *out = e;
   return GRNG_OK;
@@ -369,6 +428,13 @@ grng_status grng_engine_restore(grng_engine_t* out, const grng_engine_state* st)
     set_error("engine allocation failed");
     return GRNG_ERR_OOM;
   }
+  if (st->reserved > 6 || (st->reserved > 0 && st->kind != GRNG_MRG32K3A)) {
+    delete e;
+    set_error("state words: 0 (seed) or 1..6 for MRG32k3a");
+    return GRNG_ERR_INVALID_ARG;
+  }
+  e->nwords = st->reserved;
+  std::memcpy(e->words, st->words, sizeof(e->words));
   init_engine(e, st->kind, st->seed, st->offset_lo, st->offset_hi);
   *out = e;
   return GRNG_OK;
@@ -404,7 +470,8 @@ grng_status grng_engine_get_state(grng_engine_t e, grng_engine_state* out) {
     return GRNG_ERR_INVALID_ARG;
   }
   out->kind = e->kind;
-  out->reserved = 0;
+  out->reserved = e->nwords;
+  std::memcpy(out->words, e->words, sizeof(out->words));
   out->seed = e->seed;
   out->offset_lo = e->off_lo;
   out->offset_hi = e->off_hi;

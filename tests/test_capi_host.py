@@ -171,3 +171,21 @@ def test_batch_argument_errors(g):
     assert nbytes.value >= 256
     assert lib.grng_batch_workspace_bytes(req, 1, 0, ctypes.byref(nbytes)) == 1  # ipt out of range
     assert lib.grng_batch_destroy(None) == 0
+
+
+def test_seed_words_engines(g):
+    e = g.Engine.from_words(g.MRG32K3A, [5, 6, 7, 8], offset=100)
+    st = e.full_state
+    assert st["words"] == [5, 6, 7, 8] and st["offset"] == 100
+    r = g.Engine.restore(st)
+    assert r.full_state == st
+    p = g.Engine.from_words(g.PHILOX4X32X10, [1, 2, 3], offset=5)
+    assert p.state == (g.PHILOX4X32X10, 1 | (2 << 32), 4 * 3 + 5)
+    lib = g.load()
+    h = ctypes.c_void_p()
+    zeros = (ctypes.c_uint32 * 6)(0, 0, 0, 1, 1, 1)
+    assert lib.grng_engine_create_words(ctypes.byref(h), g.MRG32K3A, zeros, 6, 0) == 1
+    assert lib.grng_engine_create_words(ctypes.byref(h), g.MRG32K3A, zeros, 0, 0) == 1
+    assert lib.grng_engine_create_words(ctypes.byref(h), g.MRG32K3A, zeros, 7, 0) == 1
+    m = (ctypes.c_uint32 * 1)(4294967087)  # m1 = 0 mod m1
+    assert lib.grng_engine_create_words(ctypes.byref(h), g.MRG32K3A, m, 1, 0) == 0  # (1, 1, 0) is fine

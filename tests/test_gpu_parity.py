@@ -268,3 +268,22 @@ def test_generate_host_equals_device(g):
             g.generate_host(d, e2, host, work)
             assert torch.equal(dev_out.cpu().view(torch.uint8), host.view(torch.uint8)), var[0]
             assert e1.offset == e2.offset
+
+
+@pytest.mark.parametrize("engine_kind", ENGINES)
+def test_seed_word_engines(g, engine_kind):
+    """Engines seeded by word lists (including the Philox counter words and
+    MRG32k3a full states) against the oracle's independent seeding."""
+    rng = np.random.Generator(np.random.PCG64(4))
+    for count in range(1, 7):
+        words = [int(x) for x in rng.integers(1, 2**32, count)]
+        for var in [VARIANTS[0], VARIANTS[1], VARIANTS[7]]:
+            _, kind, dtype, p0, p1 = var
+            e = g.Engine.from_words(engine_kind, words, offset=3)
+            out = torch.empty(1001, dtype=_torch_dtype(dtype), device="cuda")
+            g.generate(g.Distribution(kind, dtype, p0, p1), e, out)
+            torch.cuda.synchronize()
+            ref = oracle.generate_words(engine_kind, words, 3, kind, dtype, p0, p1, 1001)
+            got = out.cpu().numpy()
+            assert_parity(kind, dtype, got.view(np.uint32) if dtype == 0 else got, ref,
+                          f"words {words} {var[0]}")

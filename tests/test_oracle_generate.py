@@ -55,3 +55,34 @@ def test_config1_head_is_stable():
     w = oracle.words(oracle.ENGINE_PHILOX, 0x12345678, 0, 1 << 20)
     assert np.array_equal(u, np.ldexp((w >> 8).astype(np.float64), -24).astype(np.float32))
     assert u.min() >= 0.0 and u.max() < 1.0
+
+
+def test_seed_words_reduce_to_single_seeds():
+    """One word (MRG) or two words (Philox) equal the single-seed engines;
+    Philox counter words equal a word offset of 4 x counter."""
+    for seed in [1, 2021, 0xFFFFFFFF, 4294967087 + 3]:
+        w32 = seed & 0xFFFFFFFF
+        a = oracle.generate_words(oracle.ENGINE_MRG, [w32], 5, DIST_BITS, DT_U32, 0, 0, 50)
+        b = oracle.generate(oracle.ENGINE_MRG, w32, 5, DIST_BITS, DT_U32, 0, 0, 50)
+        assert np.array_equal(a, b)
+    s64 = 0x0123456789ABCDEF
+    a = oracle.generate_words(0, [s64 & 0xFFFFFFFF, s64 >> 32], 9, DIST_BITS, DT_U32, 0, 0, 40)
+    b = oracle.generate(0, s64, 9, DIST_BITS, DT_U32, 0, 0, 40)
+    assert np.array_equal(a, b)
+    ctr = [7, 1, 0, 2]
+    c = sum(v << (32 * i) for i, v in enumerate(ctr))
+    a = oracle.generate_words(0, [1, 2] + ctr, 3, DIST_BITS, DT_U32, 0, 0, 40)
+    b = oracle.generate(0, 1 | (2 << 32), (4 * c + 3) % (1 << 128), DIST_BITS, DT_U32, 0, 0, 40)
+    assert np.array_equal(a, b)
+
+
+def test_mrg_seed_words_are_the_state():
+    """Six MRG words are the state: the first word follows the recursion from it."""
+    M1, M2 = 2**32 - 209, 2**32 - 22853
+    w = [11, 22, 33, 44, 55, 66]
+    x1 = [w[2], w[1], w[0]]  # (x_{-3}, x_{-2}, x_{-1})
+    x2 = [w[5], w[4], w[3]]
+    n1 = (1403580 * x1[1] - 810728 * x1[0]) % M1
+    n2 = (527612 * x2[2] - 1370589 * x2[0]) % M2
+    got = oracle.generate_words(oracle.ENGINE_MRG, w, 0, DIST_BITS, DT_U32, 0, 0, 1)
+    assert int(got[0]) == (n1 - n2) % M1
