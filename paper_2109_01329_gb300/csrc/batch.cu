@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(kThreads) batch_fill_kernel(const BatchReq* __
       case V_ICDF_GAUSS_F32: batch_tile<V_ICDF_GAUSS_F32>(r, off_lo, off_hi, g0, ipt); break;
       case V_ICDF_LOGN_F32: batch_tile<V_ICDF_LOGN_F32>(r, off_lo, off_hi, g0, ipt); break;
       case V_ICDF_GAUSS_F64: batch_tile<V_ICDF_GAUSS_F64>(r, off_lo, off_hi, g0, ipt); break;
+      case V_STDGAUSS_F64: batch_tile<V_STDGAUSS_F64>(r, off_lo, off_hi, g0, ipt); break;
       default: batch_tile<V_ICDF_LOGN_F64>(r, off_lo, off_hi, g0, ipt); break;
     }
   }

@@ -230,8 +230,9 @@ int choose_variant(const grng_distribution* d, TransformParams* t) {
       }
       t->dmean = d->p0;
       t->dsd = d->p1;
-      t->std_normal = (d->p0 == 0.0 && d->p1 == 1.0) ? 1 : 0;
-      return logn ? V_LOGN_F64 : V_GAUSS_F64;
+      if (logn) return V_LOGN_F64;
+      // fma(1, z, 0) == z, so (0, 1) drops the affine step exactly
+      return (d->p0 == 0.0 && d->p1 == 1.0) ? V_STDGAUSS_F64 : V_GAUSS_F64;
     }
     case GRNG_GAUSSIAN_ICDF:
     case GRNG_LOGNORMAL_ICDF: {

@@ -87,6 +87,22 @@ __device__ __forceinline__ uint64_t u53(uint32_t wa, uint32_t wb) {
   return ((((uint64_t)wa) << 32) | (uint64_t)wb) >> 11;
 }
 
+// The FP64 uniform x 2^-53, x = u53(w_a, w_b), in 32-bit halves.  Unless
+// x < 2^32 (probability 2^-21) the leading one of x lies in its top 21 bits
+// h = w_a >> 11: with s = clz(h) - 11, m = x << s has it at bit 52 and
+// x 2^-53 = m 2^(-53 - s), whose bit pattern is m + (1021 - s) 2^52 (the
+// leading one of m adds the missing 1 to the biased exponent 1022 - s).
+// Same value as scaled_u54_to_f64(x, -53); about a third of its operations.
+__device__ __forceinline__ double u01_f64(uint32_t wa, uint32_t wb) {
+  const uint32_t h = wa >> 11;
+  const uint32_t l = __funnelshift_r(wb, wa, 11);  // low 32 bits of x
+  if (h == 0) return scaled_u54_to_f64((uint64_t)l, -53);
+  const uint32_t s = (uint32_t)__clz(h) - 11u;     // 0..20
+  const uint32_t mh = __funnelshift_l(l, h, s);    // high half of x << s
+  const uint32_t ml = l << s;
+  return __hiloint2double((int)(mh + ((1021u - s) << 20)), (int)ml);
+}
+
 // ---------------------------------------------------------- range transform
 // Sec. 3.3, Listing 2 computes acc * (b - a) + a in a second kernel; here it
 // is fused, with explicit round-to-nearest multiply and add (never
@@ -101,12 +117,16 @@ __device__ __forceinline__ double range_f64(double u, const TransformParams& t) 
 }
 
 // -------------------------------------------------------------- Box-Muller
-// Accurate single-precision functions (no __ intrinsics): logf, sqrtf
-// (correctly rounded) and sincospif of 2 u2, which is exact.
+// Accurate single-precision logf and sincospif of 2 u2 (the argument is
+// exact); the square root is the hardware approximation (relative error
+// about 2^-23), whose argument is 0 or at least -2 ln(1 - 2^-24) > 1e-7,
+// never subnormal.
 __device__ __forceinline__ void box_muller_f32(uint32_t w0, uint32_t w1, float& z0, float& z1) {
   const float u1 = u01_open0_f32(w0);
   const float u2 = u01_f32(w1);
-  const float rho = sqrtf(-2.0f * logf(u1));
+  const float v = -2.0f * logf(u1);
+  float rho;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(rho) : "f"(v));
   float s, c;
   sincospif(2.0f * u2, &s, &c);
   z0 = rho * c;
@@ -134,11 +154,11 @@ __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
   } else if constexpr (V == V_U01_F64 || V == V_AFF_F64 || V == V_UNI_F64) {
     double r;
     if constexpr (V == V_U01_F64) {
-      r = scaled_u54_to_f64(u53(w[0], w[1]), -53);
+      r = u01_f64(w[0], w[1]);
     } else if constexpr (V == V_AFF_F64) {
       r = scaled_i54_to_f64(t.aff_a + (int64_t)u53(w[0], w[1]), t.aff_exp);
     } else {
-      r = range_f64(scaled_u54_to_f64(u53(w[0], w[1]), -53), t);
+      r = range_f64(u01_f64(w[0], w[1]), t);
     }
     const uint64_t b = (uint64_t)__double_as_longlong(r);
     o[0] = (uint32_t)b;
@@ -169,11 +189,14 @@ __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
     const uint64_t b = (uint64_t)__double_as_longlong(y);
     o[0] = (uint32_t)b;
     o[1] = (uint32_t)(b >> 32);
-  } else {  // V_GAUSS_F64, V_LOGN_F64
+  } else {  // V_GAUSS_F64, V_LOGN_F64, V_STDGAUSS_F64
     double z0, z1;
     box_muller_f64(w[0], w[1], w[2], w[3], z0, z1);
     double y0 = z0, y1 = z1;
-    if (!t.std_normal) {  // mean + sd z: fma(1, z, 0) == z, so (0, 1) skips it exactly
+    // (0, 1) is its own variant rather than a run-time branch: a branch over
+    // the two FP64 multiply-adds is predicated, and they would still issue
+    // on the narrow FP64 pipe
+    if constexpr (V != V_STDGAUSS_F64) {
       y0 = fma(t.dsd, z0, t.dmean);
       y1 = fma(t.dsd, z1, t.dmean);
     }
@@ -197,7 +220,7 @@ __device__ __forceinline__ uint4 block_outputs(uint4 b, const TransformParams& t
   constexpr int kWpu = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32 ||
                         V == V_ICDF_GAUSS_F32 || V == V_ICDF_LOGN_F32)
                            ? 1
-                       : (V == V_GAUSS_F64 || V == V_LOGN_F64) ? 4
+                       : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64) ? 4
                                                                  : 2;
   uint32_t w[4] = {b.x, b.y, b.z, b.w};
   uint32_t o[4];
@@ -211,7 +234,7 @@ struct VInfo {
   static constexpr int wpu = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32 ||
                               V == V_ICDF_GAUSS_F32 || V == V_ICDF_LOGN_F32)
                                  ? 1
-                             : (V == V_GAUSS_F64 || V == V_LOGN_F64) ? 4
+                             : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64) ? 4
                                                                        : 2;
   static constexpr int es = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32 ||
                              V == V_GAUSS_F32 || V == V_LOGN_F32 || V == V_ICDF_GAUSS_F32 ||
@@ -219,10 +242,22 @@ struct VInfo {
                                 ? 4
                                 : 8;
   static constexpr int epu = (V == V_GAUSS_F32 || V == V_LOGN_F32 || V == V_GAUSS_F64 ||
-                              V == V_LOGN_F64)
+                              V == V_LOGN_F64 || V == V_STDGAUSS_F64)
                                  ? 2
                                  : 1;
   static constexpr int ow_per_elem = es / 4;  // output words per element
+  // instruction weight of one unit: 0 a few operations, 1 a single-precision
+  // log / sincos / inverse CDF, 2 the fixed-point FP64 Box-Muller or a
+  // double-precision inverse CDF / exp (hundreds of instructions); loops
+  // over units unroll less as the weight grows, so a loop body stays in the
+  // instruction cache
+  static constexpr int weight =
+      (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64 || V == V_ICDF_GAUSS_F64 ||
+       V == V_ICDF_LOGN_F64)
+          ? 2
+      : (V == V_GAUSS_F32 || V == V_LOGN_F32 || V == V_ICDF_GAUSS_F32 || V == V_ICDF_LOGN_F32)
+          ? 1
+          : 0;
 };
 
 // 16-byte vector store (the address must be 16-byte aligned).

@@ -27,7 +27,8 @@ enum Variant : int {
   V_ICDF_LOGN_F32 = 11,
   V_ICDF_GAUSS_F64 = 12,
   V_ICDF_LOGN_F64 = 13,
-  V_COUNT = 14
+  V_STDGAUSS_F64 = 14,  // F64 gaussian with (0, 1): no FP64 affine step at all
+  V_COUNT = 15
 };
 
 // Geometry of a variant.  Every variant produces 4 output bytes per word it
@@ -45,7 +46,7 @@ inline VariantInfo variant_info(int v) {
     case V_GAUSS_F32: case V_LOGN_F32: return {4, 2, 2};
     case V_ICDF_GAUSS_F32: case V_ICDF_LOGN_F32: return {4, 1, 1};
     case V_ICDF_GAUSS_F64: case V_ICDF_LOGN_F64: return {8, 2, 1};
-    default: return {8, 4, 2};  // V_GAUSS_F64, V_LOGN_F64
+    default: return {8, 4, 2};  // V_GAUSS_F64, V_LOGN_F64, V_STDGAUSS_F64
   }
 }
 
@@ -57,7 +58,6 @@ struct TransformParams {
   double dmean, dsd;          // F64 gaussian / lognormal
   int64_t aff_a;              // F64 exact affine: r = (aff_a + x) 2^aff_exp, x = 53-bit word
   int32_t aff_exp;
-  int32_t std_normal;         // F64 gaussian / lognormal with (0, 1): skip mean + sd z
 };
 
 // One fill request as the launchers see it: num_streams streams of n

@@ -228,7 +228,8 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
     constexpr int kUpc = 4 / kWpu;          // units per 16-byte chunk
     if (active) {
       if (ub >= 0 && ub + kSu <= p.units) {
-#pragma unroll
+        constexpr int kChUnroll = VInfo<V>::weight == 0 ? 8 : VInfo<V>::weight == 1 ? 2 : 1;
+#pragma unroll kChUnroll
         for (int ch = 0; ch < 8; ++ch) {
           uint32_t o4[4];
 #pragma unroll
@@ -451,6 +452,7 @@ grng_status launch_mrg(const FillRequest& r, CUstream_st* stream) {
     case V_ICDF_LOGN_F32: return launch_variant<V_ICDF_LOGN_F32>(r, stream);
     case V_ICDF_GAUSS_F64: return launch_variant<V_ICDF_GAUSS_F64>(r, stream);
     case V_ICDF_LOGN_F64: return launch_variant<V_ICDF_LOGN_F64>(r, stream);
+    case V_STDGAUSS_F64: return launch_variant<V_STDGAUSS_F64>(r, stream);
     default: set_error("unknown variant %d", r.variant); return GRNG_ERR_INVALID_ARG;
   }
 }

@@ -299,7 +299,7 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.jf = jf;
     p.jl = jl;
     constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 4
-                       : (V == V_GAUSS_F64 || V == V_LOGN_F64)          ? 1
+                       : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64) ? 1
                                                                          : 2;
     const bool hi_uniform = base_lo + (uint64_t)groups >= base_lo;  // no carry into the top half
     auto kernel = hi_uniform ? philox_stream_kernel<V, kU, true>
@@ -387,6 +387,7 @@ grng_status launch_philox(const FillRequest& r, CUstream_st* stream) {
     case V_ICDF_LOGN_F32: return launch_variant<V_ICDF_LOGN_F32>(r, stream);
     case V_ICDF_GAUSS_F64: return launch_variant<V_ICDF_GAUSS_F64>(r, stream);
     case V_ICDF_LOGN_F64: return launch_variant<V_ICDF_LOGN_F64>(r, stream);
+    case V_STDGAUSS_F64: return launch_variant<V_STDGAUSS_F64>(r, stream);
     default: set_error("unknown variant %d", r.variant); return GRNG_ERR_INVALID_ARG;
   }
 }

@@ -72,6 +72,7 @@ grng_status launch_transform(int variant, const TransformParams& t, const uint32
     case V_ICDF_LOGN_F32: return launch_v<V_ICDF_LOGN_F32>(t, words, n, out, stream);
     case V_ICDF_GAUSS_F64: return launch_v<V_ICDF_GAUSS_F64>(t, words, n, out, stream);
     case V_ICDF_LOGN_F64: return launch_v<V_ICDF_LOGN_F64>(t, words, n, out, stream);
+    case V_STDGAUSS_F64: return launch_v<V_STDGAUSS_F64>(t, words, n, out, stream);
     default: set_error("unknown variant %d", variant); return GRNG_ERR_INVALID_ARG;
   }
 }
