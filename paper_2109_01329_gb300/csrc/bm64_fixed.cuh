@@ -1,30 +1,39 @@
-// FP64 Box-Muller in 64-bit fixed-point integer arithmetic.
+// FP64 Box-Muller in fixed-point integer arithmetic.
 //
 // The double-precision pipe of this part is narrow (a Box-Muller pair in FP64
 // math takes ~60x longer than the same pair's HBM time), so the FP64
-// gaussian is computed with 32x32 -> 64-bit integer multiplies instead, and
-// only the final result is assembled into an IEEE double (round to nearest).
+// gaussian is computed with 32-bit integer multiplies (plus one FP32 Newton
+// step) instead, and only the final result is assembled into an IEEE double
+// (round to nearest).
 //
 //   z0 = rho cos(2 pi u2), z1 = rho sin(2 pi u2), rho = sqrt(-2 ln u1),
 //   u1 = (x1 + 1) 2^-53 in (0, 1], u2 = x2 2^-53 in [0, 1), x1, x2 53-bit.
 //
-// -ln u1:  u1 = 2^-e (1 - delta) with e >= 0, delta in (0, 1/2]; a table
-//          factor c_i ~ 1/(1 - i/1024) reduces it to -ln(1 - delta) =
-//          ln c_i - ln(1 - r), 0 <= r < 2^-9, whose series r + r^2/2 + ... +
-//          r^7/7 is summed by Horner (inner terms in 32-bit fixed point).  For i = 0 (u1 within 2^-10 of 1),
-//          r = delta exactly, so -ln u1 keeps full relative accuracy even
-//          for the smallest delta, 2^-53.
-// rho:     1 / sqrt by two Newton steps from the FP32 reciprocal square root
-//          (the first one on the 24-bit seed with narrow products), then
-//          sqrt = x / sqrt(x).
+// -ln u1:  u1 = 2^-e (1 - delta), delta in (0, 1/2]; a table factor
+//          c_i ~ 1/(1 - i/1024) reduces -ln(1 - delta) to ln c_i - ln(1 - r),
+//          0 <= r < 2^-9.  The series r + r^2/2 + ... + r^6/6 takes its r^2
+//          term from 64-bit products and the r^3..r^6 terms from 32-bit high
+//          products of r 2^41 (they need 30 bits or fewer).  When e = 0 and
+//          i = 0 (u1 within 2^-10 of 1, -ln u1 below 2^-10) the whole series
+//          is evaluated relative to delta instead, so -ln u1 keeps its
+//          relative accuracy down to delta = 2^-53.
+// rho:     one FP32 Newton step for 1 / sqrt(x) from the hardware estimate,
+//          with the residual 1 - x y^2 formed exactly enough by fused
+//          multiply-adds (about 2^-43 relative), then sqrt(x) = x y corrected
+//          by the residual x - s^2 in fixed point (about 2^-57).
 // sincos:  octant symmetry, a 1025-entry table of sin / cos at multiples of
-//          2 pi / 8192 and two-term series for the residual angle
-//          phi < 2 pi 2^-13.
-// Error: below 2^-55 relative on rho and 2^-60 absolute on sin and cos
-// before the final rounding to double.
+//          2 pi / 8192, the residual angle phi < 2 pi 2^-13 through
+//          sin phi = phi - phi^3/6 and 1 - cos phi = phi^2/2 - phi^4/24
+//          (the cubic and quartic terms from 32-bit high products), and the
+//          rotation by phi as a three-product complex multiply.
+// Error budget: below 2^-51 on rho (relative, or absolute when rho < 1) and
+// 2^-57 absolute on sin and cos, so |z - exact| stays below about
+// 2^-50 max(1, |z|) before the final rounding.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "bm64_tables.h"
 
@@ -42,69 +51,58 @@ __device__ const uint32_t d_logc[GRNG_BM64_LOGC_LEN] = GRNG_BM64_LOGC;
 __device__ const uint64_t d_logt[GRNG_BM64_LOGT_LEN] = GRNG_BM64_LOGT;
 __device__ const uint64_t d_sint[GRNG_BM64_SINT_LEN] = GRNG_BM64_SINT;
 __device__ const uint64_t d_cost[GRNG_BM64_COST_LEN] = GRNG_BM64_COST;
+__device__ const uint64_t d_e58[GRNG_BM64_E58_LEN] = GRNG_BM64_E58;
 #endif
 static const uint32_t h_logc[GRNG_BM64_LOGC_LEN] = GRNG_BM64_LOGC;
 static const uint64_t h_logt[GRNG_BM64_LOGT_LEN] = GRNG_BM64_LOGT;
 static const uint64_t h_sint[GRNG_BM64_SINT_LEN] = GRNG_BM64_SINT;
 static const uint64_t h_cost[GRNG_BM64_COST_LEN] = GRNG_BM64_COST;
+static const uint64_t h_e58[GRNG_BM64_E58_LEN] = GRNG_BM64_E58;
 
-GRNG_BM_HD uint32_t logc(uint32_t i) {
 #if defined(__CUDA_ARCH__)
-  return __ldg(&d_logc[i]);
+#define GRNG_BM_TABLE(d, h, i) __ldg(&d[i])
 #else
-  return h_logc[i];
+#define GRNG_BM_TABLE(d, h, i) h[i]
 #endif
-}
-GRNG_BM_HD uint64_t logt(uint32_t i) {
+GRNG_BM_HD uint32_t logc(uint32_t i) { return GRNG_BM_TABLE(d_logc, h_logc, i); }
+GRNG_BM_HD uint64_t logt(uint32_t i) { return GRNG_BM_TABLE(d_logt, h_logt, i); }
+GRNG_BM_HD uint64_t sint(uint32_t j) { return GRNG_BM_TABLE(d_sint, h_sint, j); }
+GRNG_BM_HD uint64_t cost(uint32_t j) { return GRNG_BM_TABLE(d_cost, h_cost, j); }
+GRNG_BM_HD uint64_t e58(uint32_t e) { return GRNG_BM_TABLE(d_e58, h_e58, e); }
+#undef GRNG_BM_TABLE
+
+// 32 x 32 -> 64-bit product, and its high word.
+GRNG_BM_HD uint64_t mulw(uint32_t a, uint32_t b) { return (uint64_t)a * b; }
+GRNG_BM_HD uint32_t mulh(uint32_t a, uint32_t b) {
 #if defined(__CUDA_ARCH__)
-  return __ldg(&d_logt[i]);
+  return __umulhi(a, b);
 #else
-  return h_logt[i];
-#endif
-}
-GRNG_BM_HD uint64_t sint(uint32_t j) {
-#if defined(__CUDA_ARCH__)
-  return __ldg(&d_sint[j]);
-#else
-  return h_sint[j];
-#endif
-}
-GRNG_BM_HD uint64_t cost(uint32_t j) {
-#if defined(__CUDA_ARCH__)
-  return __ldg(&d_cost[j]);
-#else
-  return h_cost[j];
+  return (uint32_t)(((uint64_t)a * b) >> 32);
 #endif
 }
 
-GRNG_BM_HD uint64_t umulhi(uint64_t a, uint64_t b) {
-#if defined(__CUDA_ARCH__)
-  return __umul64hi(a, b);
-#else
-  return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
-#endif
-}
-
-// High 64 bits of a * b from three 32x32 -> 64-bit products: the low x low
-// product and the carry out of the low halves of the two cross products are
-// dropped, so the result is at most 2 below the exact high word (2 units of
-// the 2^-64 scale used throughout).  Where two halves of one product are
-// spliced together the exact form below is used instead.
+// High 64 bits of a * b from three 32x32 products: the low x low product and
+// the carry out of the low halves of the two cross products are dropped, so
+// the result is at most 2 below the exact high word.
 GRNG_BM_HD uint64_t umulhi_apx(uint64_t a, uint64_t b) {
-  const uint64_t ah = a >> 32, al = (uint32_t)a, bh = b >> 32, bl = (uint32_t)b;
-  return ah * bh + ((ah * bl) >> 32) + ((al * bh) >> 32);
+  const uint32_t ah = (uint32_t)(a >> 32), al = (uint32_t)a;
+  const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
+  return mulw(ah, bh) + mulh(ah, bl) + mulh(al, bh);
+}
+
+// High 64 bits of a^2 for a < 2^63: the cross product appears twice, so two
+// products suffice (at most 2 below the exact high word).
+GRNG_BM_HD uint64_t sqr_hi(uint64_t a) {
+  const uint32_t ah = (uint32_t)(a >> 32), al = (uint32_t)a;
+  return mulw(ah, ah) + mulh(ah << 1, al);
 }
 
 // Exact 96-bit product of a 64-bit and a 32-bit value: hi = (a c) >> 32,
 // lo32 = (a c) mod 2^32.
 GRNG_BM_HD void mul64x32(uint64_t a, uint32_t c, uint64_t& hi, uint32_t& lo32) {
-  const uint64_t l = (a & 0xFFFFFFFFull) * c;
-  hi = (a >> 32) * c + (l >> 32);
+  const uint64_t l = mulw((uint32_t)a, c);
+  hi = mulw((uint32_t)(a >> 32), c) + (l >> 32);
   lo32 = (uint32_t)l;
-}
-
-GRNG_BM_HD uint32_t __umulhi32(uint32_t a, uint32_t b) {
-  return (uint32_t)(((uint64_t)a * b) >> 32);
 }
 
 GRNG_BM_HD int clz64(uint64_t x) {  // x != 0
@@ -115,63 +113,131 @@ GRNG_BM_HD int clz64(uint64_t x) {  // x != 0
 #endif
 }
 
+GRNG_BM_HD uint32_t clz32(uint32_t x) {  // x != 0
+#if defined(__CUDA_ARCH__)
+  return (uint32_t)__clz((int)x);
+#else
+  return (uint32_t)__builtin_clz(x);
+#endif
+}
+
+// High word of (hi:lo) << s and low word of (hi:lo) >> s, for 0 <= s < 32.
+GRNG_BM_HD uint32_t shl_hi(uint32_t lo, uint32_t hi, uint32_t s) {
+#if defined(__CUDA_ARCH__)
+  return __funnelshift_l(lo, hi, s);
+#else
+  return s == 0 ? hi : (hi << s) | (lo >> (32 - s));
+#endif
+}
+GRNG_BM_HD uint32_t shr_lo(uint32_t lo, uint32_t hi, uint32_t s) {
+#if defined(__CUDA_ARCH__)
+  return __funnelshift_r(lo, hi, s);
+#else
+  return s == 0 ? lo : (lo >> s) | (hi << (32 - s));
+#endif
+}
+
+GRNG_BM_HD uint64_t join(uint32_t hi, uint32_t lo) { return ((uint64_t)hi << 32) | lo; }
+
+GRNG_BM_HD float bits_f32(uint32_t b) {
+  float f;
+  std::memcpy(&f, &b, 4);
+  return f;
+}
+GRNG_BM_HD uint32_t f32_bits(float f) {
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  return b;
+}
+GRNG_BM_HD float fma32(float a, float b, float c) {
+#if defined(__CUDA_ARCH__)
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fmaf(a, b, c);
+#endif
+}
+
 GRNG_BM_HD float rsqrt_seed(float x) {
 #if defined(__CUDA_ARCH__)
   return rsqrtf(x);
 #else
-  return 1.0f / __builtin_sqrtf(x);
+  return 1.0f / std::sqrt(x);
 #endif
 }
 
 // -ln(u1) for u1 = m1 2^-53, m1 in [1, 2^53), as lm 2^le with lm normalised
 // (top bit set).  m1 = 2^53 (u1 = 1) is handled by the caller.
 GRNG_BM_HD void neg_log(uint64_t m1, uint64_t& lm, int& le) {
-  const int q = 63 - clz64(m1);             // 0..52
-  const uint64_t e = (uint64_t)(52 - q);    // u1 = 2^-e (1 - delta)
-  const uint64_t M = m1 << (63 - q);        // (1 - delta) 2^64, top bit set
+  // M = m1 << s, s = clz(m1): (1 - delta) 2^64 with its top bit set, and
+  // u1 = 2^-e (1 - delta) with e = s - 11.  Except when m1 < 2^32
+  // (probability 2^-21) the shift is found from the high word alone.
+  const uint32_t m1h = (uint32_t)(m1 >> 32), m1l = (uint32_t)m1;
+  uint64_t M;
+  uint32_t e;
+  if (m1h != 0) {
+    const uint32_t s = clz32(m1h);          // 11..31
+    M = join(shl_hi(m1l, m1h, s), m1l << s);
+    e = s - 11u;
+  } else {
+    const int s = clz64(m1);                // 32..63
+    M = m1 << s;
+    e = (uint32_t)(s - 11);
+  }
   const uint64_t D = 0ull - M;              // delta 2^64 in (0, 2^63]
   const uint32_t i = (uint32_t)(D >> 54);   // 0..512
+  if (e == 0 && i == 0) {
+    // delta < 2^-10: -ln u1 = delta (1 + f), f = delta/2 + delta^2/3 + ... +
+    // delta^5/6 (delta^6/7 is below 2^-62 relative), scaled by the
+    // normalised delta so that no absolute truncation enters
+    const int nz = clz64(D);                // 10..53 (D >= 2^11)
+    const uint64_t Dn = D << nz;
+    uint64_t G = kInv6;
+    G = kInv5 + umulhi_apx(D, G);
+    G = kInv4 + umulhi_apx(D, G);
+    G = kInv3 + umulhi_apx(D, G);
+    G = kInv2 + umulhi_apx(D, G);
+    const uint64_t F = umulhi_apx(D, G);    // f 2^64
+    const uint64_t half = Dn >> 1;
+    const uint64_t Ls = half + umulhi_apx(half, F);  // -ln u1 2^(63 + nz), in [2^62, 2^64)
+    const int c = clz64(Ls);                // 0 or 1
+    lm = Ls << c;
+    le = -63 - nz - c;
+    return;
+  }
   const uint32_t C = logc(i);               // c_i 2^24
   // r 2^64 = 2^64 - M C 2^-24 (truncating M C 2^-24 leaves r >= 0); the
   // 96-bit product M C is exact, and M C 2^-24 = (hi << 8) | (lo32 >> 24)
   uint64_t mc_hi;
   uint32_t mc_lo;
   mul64x32(M, C, mc_hi, mc_lo);
-  const uint64_t R = 0ull - ((mc_hi << 8) | (uint64_t)(mc_lo >> 24));
-  // -ln(1 - r) = r + r^2 (1/2 + r (1/3 + r B4)), B4 = 1/4 + r/5 + r^2/6 + r^3/7.
-  // r < 2^-9, so r^4 B4 is below 2^-36: B4 in 32-bit fixed point (its error
-  // enters S below 2^-67), the outer two Horner steps in 64-bit.
-  const uint32_t r32 = (uint32_t)(R >> 32);             // r 2^32 < 2^23
-  uint32_t b4 = kInv7_32;
-  b4 = kInv6_32 + __umulhi32(r32, b4);
-  b4 = kInv5_32 + __umulhi32(r32, b4);
-  b4 = kInv4_32 + __umulhi32(r32, b4);
-  uint64_t b4r_hi;                                       // (R b4) >> 32 = r B4 2^64
-  uint32_t b4r_lo;
-  mul64x32(R, b4, b4r_hi, b4r_lo);
-  const uint64_t B3 = kInv3 + b4r_hi;
-  const uint64_t B2 = kInv2 + umulhi_apx(R, B3);
-  const uint64_t S = R + umulhi_apx(umulhi_apx(R, R), B2);
-  // L 2^64 = e ln 2 + ln c_i + S, as a 128-bit sum (e ln 2 exactly: 64 x 32)
-  uint64_t ln2e_hi;
-  uint32_t ln2e_lo;
-  mul64x32(kLn2, (uint32_t)e, ln2e_hi, ln2e_lo);
-  uint64_t lo = (ln2e_hi << 32) | ln2e_lo;
-  uint64_t hi = ln2e_hi >> 32;
-  const uint64_t T = logt(i);
-  lo += T;
-  hi += (lo < T) ? 1u : 0u;
-  lo += S;
-  hi += (lo < S) ? 1u : 0u;
-  if (hi != 0) {
-    const int nz = clz64(hi);               // 58..63
-    lm = (hi << nz) | (lo >> (64 - nz));
-    le = -nz;
-  } else {
-    const int nz = clz64(lo);               // lo != 0 since u1 < 1
-    lm = lo << nz;
-    le = -64 - nz;
+  const uint64_t R = 0ull - ((mc_hi << 8) | (uint64_t)(mc_lo >> 24));  // < 2^55
+  // -ln(1 - r) 2^64 = R + R^2/2 + T3 + T4 + T5 + T6 (r^7/7 < 2^-65.8).
+  // With r32 = r 2^41 the higher powers come from 32-bit high products:
+  // q = r^2 2^50, t = r^3 2^59, u = r^4 2^68, v = r^5 2^77, w = r^6 2^86.
+  const uint32_t r32 = (uint32_t)(R >> 23);
+  const uint32_t q = mulh(r32, r32);
+  const uint32_t t = mulh(q, r32);
+  const uint32_t u = mulh(q, q);
+  const uint32_t v = mulh(u, r32);
+  const uint32_t w = mulh(u, q);
+  const uint64_t T3 = mulw(t, 0xAAAAAAABu) >> 28;              // t 2^5 / 3
+  const uint32_t T456 = (u >> 6) +                              // u / 2^6
+                        (mulh(v, 0x33333333u) >> 13) +          // v / (5 2^13)
+                        (mulh(w, 0x2AAAAAABu) >> 22);           // w / (6 2^22)
+  const uint64_t S = R + (sqr_hi(R) >> 1) + T3 + T456;
+  // -ln(1 - delta) 2^64 = ln c_i 2^64 + S < ln 2 2^64 + 2^55; with e >= 1
+  // the sum e ln 2 + ... is kept in units of 2^-58 (below 37 2^58 < 2^64)
+  uint64_t Lf = logt(i) + S;
+  int lb = -64;
+  if (e != 0) {
+    Lf = e58(e) + (Lf >> 6);
+    lb = -58;
   }
+  // Lf >= 2^54 (-ln u1 >= ln c_1 > 2^-10 here), so its high word is not 0
+  const uint32_t Lh = (uint32_t)(Lf >> 32), Ll = (uint32_t)Lf;
+  const uint32_t nz = clz32(Lh);            // 0..10
+  lm = join(shl_hi(Ll, Lh, nz), Ll << nz);
+  le = lb - (int)nz;
 }
 
 // sqrt(2 lm 2^le) as sq 2^se, sq in [2^61, 2^62].
@@ -182,31 +248,33 @@ GRNG_BM_HD void sqrt2x(uint64_t lm, int le, uint64_t& sq, int& se) {
     X = lm >> 1;
     E += 1;
   }
-  // x = X 2^-64 in [1/4, 1); y = 1/sqrt(x) in (1, 2] kept as Y = y 2^62
-  const float xf = (float)(uint32_t)(X >> 40) * 0x1p-24f;
-  const float yf = rsqrt_seed(xf);
-  uint32_t yb;
-  __builtin_memcpy(&yb, &yf, 4);
-  const int ey = (int)((yb >> 23) & 0xFFu) - 127;   // 0 or 1
-  // first Newton step from the 24-bit seed y0 = m24 2^(ey - 23): its square
-  // and its product with (3 - x y0^2) need only 24 x 32 / 24 x 64 products
+  // x = X 2^-64 in [1/4, 1) as xh + xl, two 23-bit pieces (error < 2^-46)
+  const float xh = bits_f32(0x3F800000u | (uint32_t)(X >> 41)) - 1.0f;
+  const float xl = (bits_f32(0x3F800000u | ((uint32_t)(X >> 18) & 0x7FFFFFu)) - 1.0f) * 0x1p-23f;
+  // y0 ~ 1/sqrt(x) in [1, 2]; r = 1 - x y0^2 from the exact square
+  // y0^2 = p + pe, each fused step rounding at about 2^-46
+  const float y0 = rsqrt_seed(xh);
+  const float p = y0 * y0;
+  const float pe = fma32(y0, y0, -p);
+  float r = fma32(-xh, p, 1.0f);
+  r = fma32(-xh, pe, r);
+  r = fma32(-xl, p, r);
+  // y1 = y0 (1 + r/2 + 3 r^2/8): dy = y1 - y0, |dy| < 2^-20, rounded to a
+  // multiple of 2^-41 by the 1.5 2^23 shifter
+  const float dy = y0 * (r * fma32(0.375f, r, 0.5f));
+  const int32_t dyi = (int32_t)(f32_bits(fma32(dy, 0x1p41f, 12582912.0f)) - 0x4B400000u);
+  // Y1 = y1 2^62: y0 = m24 2^(ey - 23) with ey = 0 or 1 puts m24 at bit 39 + ey
+  const uint32_t yb = f32_bits(y0);
   const uint32_t m24 = (yb & 0x7FFFFFu) | 0x800000u;
-  const uint64_t Y2a = ((uint64_t)m24 * m24) << (14 + 2 * ey);  // y0^2 2^60, exact
-  const uint64_t Tma = (3ull << 60) - umulhi_apx(X, Y2a);        // (3 - x y0^2) 2^60
-  uint64_t t_hi;
-  uint32_t t_lo;
-  mul64x32(Tma, m24, t_hi, t_lo);                   // m24 Tm / 2^32
-  // y1 2^62 = y0 (3 - x y0^2) / 2 2^62 = m24 Tm 2^(ey - 23 - 60 + 61)
-  uint64_t Y = ey >= 0 ? (t_hi << (ey + 10)) | ((uint64_t)t_lo >> (22 - ey))
-                       : (t_hi << 9) | ((uint64_t)t_lo >> 23);
-  {
-    const uint64_t Y2 = umulhi_apx(Y, Y);             // y^2 2^60
-    const uint64_t XY2 = umulhi_apx(X, Y2);           // x y^2 2^60
-    const uint64_t Tm = (3ull << 60) - XY2;           // (3 - x y^2) 2^60
-    Y = umulhi_apx(Y, Tm) << 3;                       // y (3 - x y^2) / 2 2^62
-  }
-  // sqrt(x) 2^62 (kept below 2^62 + error: no shift, so no wrap near x = 1)
-  sq = umulhi_apx(X, Y);
+  const uint32_t ey = (yb >> 23) - 127u;
+  const uint64_t Y1 = join(m24 << (7u + ey), 0u) + (uint64_t)((int64_t)dyi * (int64_t)(1 << 21));
+  // s0 = x y1 ~ sqrt(x) 2^62; then s = s0 + (x - s0^2) y1 / 2, in which the
+  // residual is at most ~2^-40 x: in 2^-60 units it fits 32 bits, and
+  // (x - s0^2) 2^60 y1 / 2 in 2^-62 units is d (y1 2^30) 2^-29
+  const uint64_t s0 = umulhi_apx(X, Y1);
+  const int32_t d = (int32_t)((uint32_t)(X >> 4) - (uint32_t)sqr_hi(s0));
+  const int32_t y30 = (int32_t)(uint32_t)(Y1 >> 32);
+  sq = s0 + (uint64_t)(((int64_t)d * (int64_t)y30) >> 29);
   // sqrt(2L) = sqrt(X 2^E) = sqrt(x) 2^32 2^(E/2) = sq 2^(E/2 - 30)
   se = E / 2 - 30;
 }
@@ -220,17 +288,25 @@ GRNG_BM_HD void sincos_turns(uint64_t x2, uint64_t& c_abs, bool& c_neg, uint64_t
   const uint32_t j = (uint32_t)(t >> 40);           // 0..1024
   const uint64_t h = t & ((1ull << 40) - 1);
   const uint64_t P = umulhi_apx(h << 14, k2Pi61);   // phi 2^64 = 2 pi h 2^11 < 2^53.7
-  const uint64_t P2 = umulhi_apx(P, P);             // phi^2 2^64, < 2^43.3
-  const uint64_t P3 = umulhi_apx(P2, P);            // < 2^33
-  const uint64_t p2s = P2 >> 13;                    // phi^2 2^51, < 2^30.3
-  const uint64_t P4 = (p2s * p2s) >> 38;            // phi^4 2^64, < 2^23
-  // sin phi = phi - phi^3/6 (+ phi^5/120 < 2^-58) ;
-  // 1 - cos phi = phi^2/2 - phi^4/24 (+ phi^6/720 < 2^-71)
-  const uint64_t sphi = P - umulhi_apx(P3, kInv6);
-  const uint64_t eps = (P2 >> 1) - ((P4 * kInv24_32) >> 32);
+  const uint64_t P2 = sqr_hi(P);                    // phi^2 2^64 < 2^43.4
+  const uint32_t a = (uint32_t)(P2 >> 12);          // phi^2 2^52
+  const uint32_t b = (uint32_t)(P >> 22);           // phi 2^42
+  // phi^4/24 2^64 = (a^2 2^-32) / 6144 and phi^3/6 2^64 = (a b 2^-32) 2/3;
+  // both need under 28 significant bits (phi^5/120 2^64 < 41 is dropped)
+  const uint32_t Q4 = mulh(mulh(a, a), 699051u);
+  const uint32_t Q3 = mulh(mulh(a, b), 2863311531u);
+  const uint64_t eps = (P2 >> 1) - Q4;              // (1 - cos phi) 2^64
+  const uint64_t sphi = P - Q3;                     // sin phi 2^64, >= eps
+  // (C + iS)(1 - eps + i sphi) = C + iS + (C + iS)(-eps + i sphi), the last
+  // product as k1 = eps (C + S), k2 = C (sphi + eps), k3 = S (sphi - eps):
+  // cos = C - k1 - k3, sin = S + k2 - k1
   const uint64_t Sj = sint(j), Cj = cost(j);
-  const uint64_t sn = Sj - umulhi_apx(Sj, eps) + umulhi_apx(Cj, sphi);  // sin(alpha + phi) 2^63
-  const uint64_t cs = Cj - umulhi_apx(Cj, eps) - umulhi_apx(Sj, sphi);  // cos(alpha + phi) 2^63
+  const uint64_t k1 = umulhi_apx(Cj + Sj, eps);
+  const uint64_t k2 = umulhi_apx(Cj, sphi + eps);
+  const uint64_t k3 = umulhi_apx(Sj, sphi - eps);
+  const uint64_t cs = Cj - k1 - k3;                 // cos(alpha + phi) 2^63 >= 2^62.5
+  const int64_t snv = (int64_t)(Sj + k2 - k1);      // sin(alpha + phi) 2^63, >= -2
+  const uint64_t sn = snv < 0 ? 0ull : (uint64_t)snv;
   const bool swap = ((o + 1u) & 2u) != 0;           // octants 1, 2, 5, 6
   s_abs = swap ? cs : sn;
   c_abs = swap ? sn : cs;
@@ -239,21 +315,30 @@ GRNG_BM_HD void sincos_turns(uint64_t x2, uint64_t& c_abs, bool& c_neg, uint64_t
 }
 
 // p 2^k as a double, rounded to nearest (ties away), with sign; p = 0 gives +0.
+// With m = p << s (top bit set), the 53-bit significand is (m >> 11) plus
+// the rounding bit (m >> 10) & 1, and the bit pattern is that significand
+// plus (E - 1) 2^52, E = 1086 - s + k the biased exponent: the significand's
+// leading one supplies the missing 1, and a carry out of rounding (all ones
+// rounded up) moves into the exponent by itself.
 GRNG_BM_HD double assemble(uint64_t p, int k, bool neg) {
-  if (p == 0) return 0.0;
-  const int nz = clz64(p);
-  uint64_t m = p << nz;                             // top bit set
-  uint64_t mant = m >> 11;                          // 53 bits
-  mant += (m >> 10) & 1u;                           // round half away from zero
-  int ex = 63 - nz + k;
-  if (mant >> 53) {
-    mant >>= 1;
-    ex += 1;
+  const uint32_t ph = (uint32_t)(p >> 32), pl = (uint32_t)p;
+  uint32_t mh, ml, s;
+  if (ph != 0) {
+    s = clz32(ph);
+    mh = shl_hi(pl, ph, s);
+    ml = pl << s;
+  } else {                                          // p < 2^32 (|z| < 2^-29)
+    if (pl == 0) return 0.0;
+    const uint32_t t = clz32(pl);
+    s = 32u + t;
+    mh = pl << t;
+    ml = 0u;
   }
-  const uint64_t bits = ((uint64_t)(ex + 1023) << 52) | (mant & ((1ull << 52) - 1)) |
-                        (neg ? (1ull << 63) : 0ull);
+  const uint32_t hi = (mh >> 11) + ((uint32_t)(1085 + k - (int)s) << 20) +
+                      (neg ? 0x80000000u : 0u);
+  const uint64_t bits = join(hi, shr_lo(ml, mh, 11)) + ((ml >> 10) & 1u);
   double d;
-  __builtin_memcpy(&d, &bits, 8);
+  std::memcpy(&d, &bits, 8);
   return d;
 }
 

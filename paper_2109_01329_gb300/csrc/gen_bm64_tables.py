@@ -8,6 +8,7 @@ Tables (emitted as initializer macros GRNG_BM64_LOGC, _LOGT, _SINT, _COST)
                          factor for -ln(1 - delta) with delta in [i/1024, (i+1)/1024)
   kLogT[i]:              ln(c_i) * 2^64 (c_i exactly as stored)
   kSinT[j], kCosT[j], j = 0..1024:  sin, cos(2 pi j / 8192) * 2^63
+  kE58[e], e = 0..52:    e ln 2 * 2^58
 Scalars
   kLn2:    ln 2 * 2^64
   k2Pi61:  2 pi * 2^61
@@ -44,6 +45,8 @@ def main():
     assert all(t < 1 << 64 for t in logt)
     sint = [rnd(mp.sin(2 * mp.pi * j / 8192) * two63) for j in range(1025)]
     cost = [rnd(mp.cos(2 * mp.pi * j / 8192) * two63) for j in range(1025)]
+    e58 = [rnd(e * mp.log(2) * mp.mpf(2) ** 58) for e in range(53)]
+    assert all(v < 1 << 64 for v in e58)
 
     out.append(f"constexpr uint64_t kLn2 = {rnd(mp.log(2) * two64)}ull;")
     out.append(f"constexpr uint64_t k2Pi61 = {rnd(2 * mp.pi * mp.mpf(2) ** 61)}ull;")
@@ -56,7 +59,8 @@ def main():
     out.append(f"constexpr uint32_t kInv720_32 = {rnd(mp.mpf(2) ** 32 / 720)}u;")
     # table bodies as macros: the device and host copies are declared where used
     for name, ctype, vals in [("LOGC", "uint32_t", logc), ("LOGT", "uint64_t", logt),
-                              ("SINT", "uint64_t", sint), ("COST", "uint64_t", cost)]:
+                              ("SINT", "uint64_t", sint), ("COST", "uint64_t", cost),
+                              ("E58", "uint64_t", e58)]:
         suffix = "ull" if "64" in ctype else "u"
         out.append(f"#define GRNG_BM64_{name}_LEN {len(vals)}")
         out.append(f"#define GRNG_BM64_{name} {{ \\")
