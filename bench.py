@@ -202,15 +202,17 @@ def oracle_rate(seconds_per_case: float, cores: int, n_cap: int):
 # implemented: Philox4x32-10 is 20 products per 4-word block; an MRG32k3a word
 # is 9 (per component two multiplier products, then the folds of 2^32 = c
 # mod m: one wide fold and one carry fold for m1, two wide folds and one
-# carry fold for m2); the fixed-point FP64 Box-Muller pair is 82 products
-# (24 three-product high multiplies, two exact 64x32 products, 6 small 32-bit
-# products) on top of the products of its 4 words.
+# carry fold for m2); the fixed-point FP64 Box-Muller pair is 42 products
+# (log: 12, square root: 6, sine and cosine: 18, the two final products: 6)
+# on top of the products of its 4 words.
+BM64_PRODUCTS_PER_PAIR = 42
 PRODUCTS_PER_SAMPLE = {
     "philox4x32_10/bits_u32": 5, "philox4x32_10/uniform_f32": 5,
     "philox4x32_10/uniform_f64": 10, "philox4x32_10/gaussian_f32": 5,
-    "philox4x32_10/gaussian_f64": (20 + 82) / 2, "philox4x32_10/lognormal_f32": 5,
+    "philox4x32_10/gaussian_f64": (20 + BM64_PRODUCTS_PER_PAIR) / 2,
+    "philox4x32_10/lognormal_f32": 5,
     "mrg32k3a/bits_u32": 9, "mrg32k3a/uniform_f32": 9, "mrg32k3a/uniform_f64": 18,
-    "mrg32k3a/gaussian_f32": 9, "mrg32k3a/gaussian_f64": (36 + 82) / 2,
+    "mrg32k3a/gaussian_f32": 9, "mrg32k3a/gaussian_f64": (36 + BM64_PRODUCTS_PER_PAIR) / 2,
     "mrg32k3a/lognormal_f32": 9,
 }
 
@@ -583,11 +585,25 @@ def run_ours(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
         d2h = sum(n * (8 if d[2] == 2 else 4) for _, _, d in cases)
+        # the device -> pinned host link alone: one 2 GiB copy, three times
+        link_bytes = min(host.numel(), 2 << 30)
+        src = torch.empty(link_bytes, dtype=torch.uint8, device=dev)
+        host[:link_bytes].copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(3):
+            host[:link_bytes].copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        link_gbs = 3 * link_bytes / (time.perf_counter() - t1) / 1e9
+        del src
+        e2e_gbs = d2h * args.e2e_steps / dt / 1e9
         e2e = {"value": samples_per_step * args.e2e_steps / dt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
                "ms_per_step": dt / args.e2e_steps * 1e3,
+               "d2h_gbs": round(e2e_gbs, 1), "link_gbs": round(link_gbs, 1),
+               "frac_link": round(e2e_gbs / link_gbs, 4),
                "how": "grng_generate_host into pinned host memory, 256 MiB device staging, "
-                      "host wall clock"}
+                      "host wall clock; link_gbs is a plain 2 GiB device-to-pinned-host copy"}
         del host, work
 
     batched = None

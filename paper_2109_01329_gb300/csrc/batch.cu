@@ -16,10 +16,9 @@
 // generator's sequence with no host work.  grng_batch_commit copies the device
 // offsets back into the engines.
 //
-// Groups whose words start on a Philox block boundary and whose units do not
-// straddle the group (every group of a request whose word offset matches its
-// pointer's 16-byte phase) take the one-block path; any other phase computes
-// the two or three blocks its words span.
+// A request whose word offset matches its pointer's 16-byte phase maps each
+// 16-byte group to one Philox block; any other phase stages the blocks of a
+// slice of groups in shared memory and assembles the groups from there.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -44,85 +43,109 @@ constexpr int kThreads = 256;
 //   BatchReq reqs[count] | uint64_t off[count][2] | int32_t tile_req[tiles]
 size_t align256(size_t x) { return (x + 255u) & ~(size_t)255u; }
 
+// Blocks staged per slice of kThreads groups: 1024 words, up to wpu - 1 words
+// of a unit straddling each end, the phase, block rounding.
+constexpr int kSliceBlocks = kThreads + 4;
+
+// Stores the elements of group (first element e0) that lie in [0, n).
 template <int V>
-__device__ __forceinline__ void batch_group(const BatchReq& r, uint64_t off_lo, uint64_t off_hi,
-                                            int64_t g) {
+__device__ __forceinline__ void store_group(char* base, int64_t e0, int64_t n, uint4 o) {
   using I = VInfo<V>;
   constexpr int kEpg = 16 / I::es;
-  constexpr int kWpu = I::wpu, kEpu = I::epu, kOwpe = I::ow_per_elem;
-  const int64_t e0 = g * kEpg - r.head;
-  const int64_t lo_e = e0 > 0 ? e0 : 0;
-  const int64_t hi_e = (e0 + kEpg) < r.n ? (e0 + kEpg) : r.n;
-  if (lo_e >= hi_e) return;
-  const int64_t k_lo = lo_e / kEpu, k_hi = (hi_e - 1) / kEpu;
-  // first word of unit k_lo (128-bit)
-  uint64_t w_lo = off_lo + (uint64_t)(k_lo * kWpu);
-  uint64_t w_hi = off_hi + ((w_lo < off_lo) ? 1u : 0u);
-  const uint32_t ph = (uint32_t)(w_lo & 3u);
-  const uint64_t b_lo = (w_lo >> 2) | (w_hi << 62), b_hi = w_hi >> 2;
-  char* base = reinterpret_cast<char*>(r.out);
-  const bool full = (lo_e == e0) && (hi_e == e0 + kEpg);
-  const int nwords = (int)((k_hi - k_lo + 1) * kWpu);
-  if (full && ph == 0 && nwords == 4) {
-    // the group is exactly one block
-    const uint4 o = block_outputs<V>(philox4x32_10(ctr_from(b_lo, b_hi), r.key0, r.key1), r.t);
+  if (e0 >= 0 && e0 + kEpg <= n) {
     store16(base + e0 * I::es, o);
     return;
   }
-  // general phase: up to 3 blocks cover the (at most 4 + wpu) words
-  uint32_t w[12];
-  const int nb = (int)((ph + nwords + 3) >> 2);
+  const uint32_t ow[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    if (b < nb) {
-      uint64_t c_lo = b_lo + (uint64_t)b;
-      const uint64_t c_hi = b_hi + ((c_lo < b_lo) ? 1u : 0u);
-      const uint4 blk = philox4x32_10(ctr_from(c_lo, c_hi), r.key0, r.key1);
-      w[4 * b + 0] = blk.x;
-      w[4 * b + 1] = blk.y;
-      w[4 * b + 2] = blk.z;
-      w[4 * b + 3] = blk.w;
-    }
-  }
-  uint32_t gout[4] = {0u, 0u, 0u, 0u};
-  for (int64_t k = k_lo; k <= k_hi; ++k) {
-    uint32_t uw[kWpu];
-#pragma unroll
-    for (int i = 0; i < kWpu; ++i) uw[i] = w[ph + (int)(k - k_lo) * kWpu + i];
-    uint32_t o[kWpu];
-    unit_outputs<V>(uw, o, r.t);
-#pragma unroll
-    for (int sl = 0; sl < kEpu; ++sl) {
-      const int64_t e = k * kEpu + sl;
-      if (e >= e0 && e < e0 + kEpg) {
-#pragma unroll
-        for (int i = 0; i < kOwpe; ++i) gout[(int)(e - e0) * kOwpe + i] = o[sl * kOwpe + i];
-      }
-    }
-  }
-  if (full) {
-    store16(base + e0 * I::es, make_uint4(gout[0], gout[1], gout[2], gout[3]));
-  } else {
-#pragma unroll
-    for (int i = 0; i < kEpg; ++i) {
-      const int64_t e = e0 + i;
-      if (e >= lo_e && e < hi_e) {
-        if constexpr (I::es == 4) {
-          reinterpret_cast<uint32_t*>(base)[e] = gout[i];
-        } else {
-          reinterpret_cast<uint2*>(base)[e] = make_uint2(gout[2 * i], gout[2 * i + 1]);
-        }
+  for (int i = 0; i < kEpg; ++i) {
+    const int64_t e = e0 + i;
+    if (e >= 0 && e < n) {
+      if constexpr (I::es == 4) {
+        reinterpret_cast<uint32_t*>(base)[e] = ow[i];
+      } else {
+        reinterpret_cast<uint2*>(base)[e] = make_uint2(ow[2 * i], ow[2 * i + 1]);
       }
     }
   }
 }
 
+// The groups [g0, g0 + kThreads ipt) of one request (the whole CTA works on
+// one tile, so every branch below is uniform across it).  Group 0 starts
+// head elements (pw = head es / 4 words) before the output; when off - pw is
+// a multiple of 4 and pw of the unit size, group g is exactly Philox block
+// (off - pw)/4 + g.  Otherwise each slice of kThreads groups stages the
+// blocks its words span in shared memory (about one block per thread) and
+// each thread assembles its group from there.
 template <int V>
 __device__ __forceinline__ void batch_tile(const BatchReq& r, uint64_t off_lo, uint64_t off_hi,
-                                           int64_t g0, int ipt) {
+                                           int64_t g0, int ipt, uint4* sblocks) {
+  using I = VInfo<V>;
+  constexpr int kEpg = 16 / I::es;
+  constexpr int kWpu = I::wpu, kEpu = I::epu, kOwpe = I::ow_per_elem;
+  const int64_t n = r.n, groups = r.groups, head = r.head;
+  const uint32_t k0 = r.key0, k1 = r.key1;
+  char* base = reinterpret_cast<char*>(r.out);
+  const TransformParams t = r.t;
+  const uint32_t pw = (uint32_t)head * (uint32_t)(I::es / 4);
+  if (((off_lo - pw) & 3u) == 0 && (pw % (uint32_t)kWpu) == 0) {
+    const uint64_t a_lo = off_lo - pw, a_hi = off_hi - ((off_lo < pw) ? 1u : 0u);
+    const uint64_t b_lo = (a_lo >> 2) | (a_hi << 62), b_hi = a_hi >> 2;
+    for (int i = 0; i < ipt; ++i) {
+      const int64_t g = g0 + (int64_t)i * kThreads + threadIdx.x;
+      if (g >= groups) break;
+      const uint64_t c_lo = b_lo + (uint64_t)g;
+      const uint64_t c_hi = b_hi + ((c_lo < b_lo) ? 1u : 0u);
+      const uint4 o = block_outputs<V>(philox4x32_10(ctr_from(c_lo, c_hi), k0, k1), t);
+      store_group<V>(base, g * kEpg - head, n, o);
+    }
+    return;
+  }
+  const uint32_t* swords = reinterpret_cast<const uint32_t*>(sblocks);
   for (int i = 0; i < ipt; ++i) {
-    const int64_t g = g0 + (int64_t)i * kThreads + threadIdx.x;
-    if (g < r.groups) batch_group<V>(r, off_lo, off_hi, g);
+    const int64_t gs = g0 + (int64_t)i * kThreads;  // first group of the slice
+    if (gs >= groups) break;
+    // elements of the slice clipped to [0, n), their units and words
+    const int64_t te0 = gs * kEpg - head;
+    const int64_t lo_e = te0 < 0 ? 0 : te0;
+    const int64_t hi_e = (te0 + kThreads * kEpg) < n ? (te0 + kThreads * kEpg) : n;
+    const int64_t k_lo = lo_e / kEpu, k_hi = (hi_e - 1) / kEpu;
+    const uint64_t w_lo = off_lo + (uint64_t)(k_lo * kWpu);
+    const uint64_t w_hi = off_hi + ((w_lo < off_lo) ? 1u : 0u);
+    const uint32_t wphase = (uint32_t)(w_lo & 3u);
+    const uint64_t b_lo = (w_lo >> 2) | (w_hi << 62), b_hi = w_hi >> 2;
+    const int nblocks = (int)((wphase + (k_hi - k_lo + 1) * kWpu + 3) >> 2);  // <= kSliceBlocks
+    for (int j = threadIdx.x; j < nblocks; j += kThreads) {
+      const uint64_t c_lo = b_lo + (uint64_t)j;
+      const uint64_t c_hi = b_hi + ((c_lo < b_lo) ? 1u : 0u);
+      sblocks[j] = philox4x32_10(ctr_from(c_lo, c_hi), k0, k1);
+    }
+    __syncthreads();
+    const int64_t e0 = te0 + (int64_t)threadIdx.x * kEpg;
+    const int64_t ge_lo = e0 < 0 ? 0 : e0;
+    const int64_t ge_hi = (e0 + kEpg) < n ? (e0 + kEpg) : n;
+    if (ge_lo < ge_hi) {
+      uint32_t gout[4] = {0u, 0u, 0u, 0u};
+      const int64_t ku_lo = ge_lo / kEpu, ku_hi = (ge_hi - 1) / kEpu;
+      for (int64_t k = ku_lo; k <= ku_hi; ++k) {
+        const int rel = (int)wphase + (int)(k - k_lo) * kWpu;
+        uint32_t w[kWpu];
+#pragma unroll
+        for (int q = 0; q < kWpu; ++q) w[q] = swords[rel + q];
+        uint32_t o[kWpu];
+        unit_outputs<V>(w, o, t);
+#pragma unroll
+        for (int sl = 0; sl < kEpu; ++sl) {
+          const int64_t e = k * kEpu + sl;
+          if (e >= e0 && e < e0 + kEpg) {
+#pragma unroll
+            for (int q = 0; q < kOwpe; ++q) gout[(int)(e - e0) * kOwpe + q] = o[sl * kOwpe + q];
+          }
+        }
+      }
+      store_group<V>(base, e0, n, make_uint4(gout[0], gout[1], gout[2], gout[3]));
+    }
+    __syncthreads();
   }
 }
 
@@ -130,27 +153,28 @@ __global__ void __launch_bounds__(kThreads) batch_fill_kernel(const BatchReq* __
                                                               const uint64_t* __restrict__ off,
                                                               const int32_t* __restrict__ tile_req,
                                                               int64_t tiles, int ipt) {
+  __shared__ uint4 sblocks[kSliceBlocks];
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int32_t ri = tile_req[t];
     const BatchReq& r = reqs[ri];
     const uint64_t off_lo = off[2 * ri], off_hi = off[2 * ri + 1];
     const int64_t g0 = (t - r.first_tile) * (int64_t)kThreads * ipt;
     switch (r.variant) {  // uniform per tile
-      case V_BITS: batch_tile<V_BITS>(r, off_lo, off_hi, g0, ipt); break;
-      case V_U01_F32: batch_tile<V_U01_F32>(r, off_lo, off_hi, g0, ipt); break;
-      case V_UNI_F32: batch_tile<V_UNI_F32>(r, off_lo, off_hi, g0, ipt); break;
-      case V_U01_F64: batch_tile<V_U01_F64>(r, off_lo, off_hi, g0, ipt); break;
-      case V_AFF_F64: batch_tile<V_AFF_F64>(r, off_lo, off_hi, g0, ipt); break;
-      case V_UNI_F64: batch_tile<V_UNI_F64>(r, off_lo, off_hi, g0, ipt); break;
-      case V_GAUSS_F32: batch_tile<V_GAUSS_F32>(r, off_lo, off_hi, g0, ipt); break;
-      case V_LOGN_F32: batch_tile<V_LOGN_F32>(r, off_lo, off_hi, g0, ipt); break;
-      case V_GAUSS_F64: batch_tile<V_GAUSS_F64>(r, off_lo, off_hi, g0, ipt); break;
-      case V_LOGN_F64: batch_tile<V_LOGN_F64>(r, off_lo, off_hi, g0, ipt); break;
-      case V_ICDF_GAUSS_F32: batch_tile<V_ICDF_GAUSS_F32>(r, off_lo, off_hi, g0, ipt); break;
-      case V_ICDF_LOGN_F32: batch_tile<V_ICDF_LOGN_F32>(r, off_lo, off_hi, g0, ipt); break;
-      case V_ICDF_GAUSS_F64: batch_tile<V_ICDF_GAUSS_F64>(r, off_lo, off_hi, g0, ipt); break;
-      case V_STDGAUSS_F64: batch_tile<V_STDGAUSS_F64>(r, off_lo, off_hi, g0, ipt); break;
-      default: batch_tile<V_ICDF_LOGN_F64>(r, off_lo, off_hi, g0, ipt); break;
+      case V_BITS: batch_tile<V_BITS>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_U01_F32: batch_tile<V_U01_F32>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_UNI_F32: batch_tile<V_UNI_F32>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_U01_F64: batch_tile<V_U01_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_AFF_F64: batch_tile<V_AFF_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_UNI_F64: batch_tile<V_UNI_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_GAUSS_F32: batch_tile<V_GAUSS_F32>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_LOGN_F32: batch_tile<V_LOGN_F32>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_GAUSS_F64: batch_tile<V_GAUSS_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_LOGN_F64: batch_tile<V_LOGN_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_ICDF_GAUSS_F32: batch_tile<V_ICDF_GAUSS_F32>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_ICDF_LOGN_F32: batch_tile<V_ICDF_LOGN_F32>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_ICDF_GAUSS_F64: batch_tile<V_ICDF_GAUSS_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_STDGAUSS_F64: batch_tile<V_STDGAUSS_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      default: batch_tile<V_ICDF_LOGN_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
     }
   }
 }

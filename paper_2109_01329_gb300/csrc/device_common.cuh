@@ -75,11 +75,12 @@ __device__ __forceinline__ double scaled_u54_to_f64(uint64_t x, int e) {
   return __longlong_as_double((long long)((bexp << 52) | frac));
 }
 
-// Signed form: v 2^e for |v| <= 2^53.
+// Signed form: v 2^e for |v| <= 2^53.  The sign goes in as a bit: negating
+// the double would be an FP64 instruction.
 __device__ __forceinline__ double scaled_i54_to_f64(int64_t v, int e) {
   const uint64_t mag = v < 0 ? (uint64_t)(-v) : (uint64_t)v;
-  const double r = scaled_u54_to_f64(mag, e);
-  return v < 0 ? -r : r;
+  const uint64_t bits = (uint64_t)__double_as_longlong(scaled_u54_to_f64(mag, e));
+  return __longlong_as_double((long long)(bits | (v < 0 ? (1ull << 63) : 0ull)));
 }
 
 // The 53-bit integer of an FP64 uniform: ((w_a << 32) | w_b) >> 11.
