@@ -206,6 +206,14 @@ def oracle_rate(seconds_per_case: float, cores: int, n_cap: int):
 # (log: 12, square root: 6, sine and cosine: 18, the two final products: 6)
 # on top of the products of its 4 words.
 BM64_PRODUCTS_PER_PAIR = 42
+
+# DRAM bytes (read + write) per launch at n = 10^9 from ncu captures of the
+# current kernels: one launch of 2.68e8 samples scaled by 1e9 / 2.68e8
+# (profiles/gaussian_f64_2.68e8_full.md); replaced when a kernel changes.
+NCU_TRAFFIC_PER_1E9 = {
+    "mrg32k3a/gaussian_f64": (2.083704e9 + 1.169e6) / 0.268,
+    "philox4x32_10/gaussian_f64": (2.083143e9 + 0.298e6) / 0.268,
+}
 PRODUCTS_PER_SAMPLE = {
     "philox4x32_10/bits_u32": 5, "philox4x32_10/uniform_f32": 5,
     "philox4x32_10/uniform_f64": 10, "philox4x32_10/gaussian_f32": 5,
@@ -515,16 +523,20 @@ def run_ours(args):
                            "frac_roofline": round((n / (ms * 1e-3)) / min(hbm_cap, int_cap), 4)}
     dom_name = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     dom = per_kernel[dom_name]
+    traffic = args.traffic
+    if traffic is None and dom_name in NCU_TRAFFIC_PER_1E9:
+        traffic = round(NCU_TRAFFIC_PER_1E9[dom_name] * n / 1e9)
     if dom["bound"] == "hbm":
         roofline = {"kernel": dom_name, "bound": "hbm", "achieved": dom["write_gbs"],
                     "peak": hbm_peak, "unit": "GB/s", "frac": dom["frac_hbm"],
-                    "traffic": args.traffic, "peak_source": f"{peak_src} hbm_gbs (copy)",
+                    "traffic": traffic, "peak_source": f"{peak_src} hbm_gbs (copy)",
                     "bytes_per_launch": n * (8 if "f64" in dom_name else 4)}
     else:
         roofline = {"kernel": dom_name, "bound": "alu", "achieved": dom["tproducts_s"],
                     "peak": round(mul_rate / 1e12, 3), "unit": "T products/s (32x32->64)",
-                    "frac": dom["frac_int"], "traffic": args.traffic,
-                    "peak_source": "measured live: dependent 32x32->64 multiply chains, all SMs",
+                    "frac": dom["frac_int"], "traffic": traffic,
+                    "peak_source": "measured live: the faster of two independent-chain "
+                                   "32x32->64 multiply shapes, all SMs",
                     "products_per_launch": dom["products_per_launch"],
                     "bytes_per_launch": n * (8 if "f64" in dom_name else 4)}
     target = per_kernel.get("philox4x32_10/uniform_f32", dom)
