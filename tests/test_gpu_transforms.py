@@ -76,6 +76,15 @@ def _fp64_edge_pairs(seed=1, n_random=100000):
             m1 = (1 << 53) - i * (1 << 43) + d
             if 1 <= m1 <= (1 << 53):
                 e1.append(m1 - 1)
+    # u1 just below 1, every octave of delta = 1 - u1 (the relative-accuracy
+    # branch of -ln u1 below 2^-10 and its boundary), and u1 around 1/2
+    for k in range(0, 53):
+        for d in (-1, 0, 1, 3):
+            v = M53 - ((1 << k) + d)
+            if 0 <= v <= M53:
+                e1.append(v)
+    for d in range(-40, 41):
+        e1.append((1 << 52) - 1 + d)
     e2 = [0, 1, M53, M53 - 1]
     for o in range(9):
         for d in (-2, -1, 0, 1, 2):
