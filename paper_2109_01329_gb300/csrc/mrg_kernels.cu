@@ -250,6 +250,20 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
     }
     __syncwarp();
     if constexpr (kAligned) {
+      // interior sub-chunks (every row present and inside the stream, the
+      // common case) store without per-row checks
+      const int64_t ow0 = ow_lane + q * kRowWords;
+      const bool inside = ow0 >= 0 && ow0 + 7 * row_stride + 4 <= p.out_words;
+      if (__all_sync(0xFFFFFFFFu, inside && rows_active == 32)) {
+        uint32_t* dst = stream_out + ow0;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int r = it * 4 + (lane >> 3);
+          store16(dst + it * row_stride, stage[warp][r][(lane & 7) ^ (r & 7)]);
+        }
+        __syncwarp();
+        continue;
+      }
 #pragma unroll
       for (int it = 0; it < 8; ++it) {
         const int r = it * 4 + (lane >> 3);
