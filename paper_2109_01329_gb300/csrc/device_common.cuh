@@ -57,10 +57,6 @@ __device__ __forceinline__ void add128(uint64_t& lo, uint64_t& hi, uint64_t v) {
 __device__ __forceinline__ float u01_f32(uint32_t w) {
   return __uint2float_rn(w >> 8) * 0x1p-24f;
 }
-// Box-Muller's first input: ((w >> 8) + 1) 2^-24 in (0, 1].
-__device__ __forceinline__ float u01_open0_f32(uint32_t w) {
-  return __uint2float_rn((w >> 8) + 1u) * 0x1p-24f;
-}
 
 // x 2^e for an integer 0 <= x <= 2^53, built with integer operations only
 // (exact: x has at most 53 significant bits, or is 2^53, and the result is a
@@ -118,18 +114,71 @@ __device__ __forceinline__ double range_f64(double u, const TransformParams& t) 
 }
 
 // -------------------------------------------------------------- Box-Muller
-// Accurate single-precision logf and sincospif of 2 u2 (the argument is
-// exact); the square root is the hardware approximation (relative error
-// about 2^-23), whose argument is 0 or at least -2 ln(1 - 2^-24) > 1e-7,
-// never subnormal.
+// FP32 pieces from the exact integers of u1 and u2; the polynomial
+// coefficients come from gen_bm32_poly.py (fits on Chebyshev nodes refined
+// towards minimax, rounded to float).
+//
+// -2 ln u1 for u1 = j 2^-24, j = (w >> 8) + 1 in [1, 2^24]: j = 2^e m with m
+// in [sqrt(1/2), sqrt(2)) split from the float's bits, t = m - 1 (exact),
+// ln m = t + t^2 P(t) (P of degree 7, relative error below 3e-8), and
+// -2 ln u1 = 2 ((24 - e) ln 2 - ln m): no cancellation as u1 -> 1 (e = 24).
+// Over all 2^24 inputs the relative error stays below 1e-7.
+__device__ __forceinline__ float neg2_log_u1_f32(uint32_t w) {
+  const float f = __uint2float_rn((w >> 8) + 1u);  // exact
+  const int ix = __float_as_int(f);
+  const int e = (ix - 0x3F3504F3) >> 23;
+  const float t = __int_as_float(ix - (e << 23)) - 1.0f;
+  float p = 0.08734750747680664f;
+  p = fmaf(p, t, -0.14307482540607452f);
+  p = fmaf(p, t, 0.14917989075183868f);
+  p = fmaf(p, t, -0.165705144405365f);
+  p = fmaf(p, t, 0.19962070882320404f);
+  p = fmaf(p, t, -0.25001755356788635f);
+  p = fmaf(p, t, 0.33333951234817505f);
+  p = fmaf(p, t, -0.49999991059303284f);
+  const float lnm = fmaf(t * t, p, t);
+  // 24 - e in [0, 24] as a float by the 2^23 shifter
+  const float k = __int_as_float(0x4B000000 + 24 - e) - 8388608.0f;
+  return 2.0f * fmaf(k, 0.693147182464599609375f, -lnm);
+}
+
+// sin and cos of 2 pi k 2^-24, k = w >> 8: octant o = k >> 21, the position
+// t in [0, 2^21] within it (reflected in odd octants), v = t 2^-21 (exact),
+// sin(pi v / 4) = v S(v^2) and cos(pi v / 4) = 1 + v^2 C(v^2) (fit errors
+// 2.4e-9 relative and 5.4e-11); at most 8.5e-8 from the exact values over
+// all 2^24 angles.
+__device__ __forceinline__ void sincos_turns_f32(uint32_t w, float& s, float& c) {
+  const uint32_t k = w >> 8;
+  const uint32_t o = k >> 21;
+  uint32_t t = k & 0x1FFFFFu;
+  if (o & 1u) t = 0x200000u - t;
+  const float v = (__int_as_float(0x4B000000u | t) - 8388608.0f) * 0x1p-21f;
+  const float ww = v * v;
+  const float sn =
+      v * fmaf(fmaf(fmaf(-3.595459565985948e-05f, ww, 0.0024900073185563087f), ww,
+                    -0.08074543625116348f),
+               ww, 0.7853981852531433f);
+  const float cs =
+      fmaf(ww,
+           fmaf(fmaf(fmaf(3.531334868966951e-06f, ww, -0.00032594200456514955f), ww,
+                     0.015854327008128166f),
+                ww, -0.3084251284599304f),
+           1.0f);
+  const bool swap = ((o + 1u) & 2u) != 0;  // octants 1, 2, 5, 6
+  const float a = swap ? cs : sn, b = swap ? sn : cs;
+  s = (o >= 4u) ? -a : a;
+  c = (((o + 2u) & 4u) != 0) ? -b : b;  // octants 2, 3, 4, 5
+}
+
+// rho = sqrt(-2 ln u1) by the hardware square root (relative error about
+// 2^-23; its argument is 0 or at least -2 ln(1 - 2^-24) > 1e-7, never
+// subnormal), z0 = rho cos(2 pi u2), z1 = rho sin(2 pi u2).
 __device__ __forceinline__ void box_muller_f32(uint32_t w0, uint32_t w1, float& z0, float& z1) {
-  const float u1 = u01_open0_f32(w0);
-  const float u2 = u01_f32(w1);
-  const float v = -2.0f * logf(u1);
+  const float v = neg2_log_u1_f32(w0);
   float rho;
   asm("sqrt.approx.f32 %0, %1;" : "=f"(rho) : "f"(v));
   float s, c;
-  sincospif(2.0f * u2, &s, &c);
+  sincos_turns_f32(w1, s, c);
   z0 = rho * c;
   z1 = rho * s;
 }
