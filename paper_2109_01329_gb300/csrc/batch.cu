@@ -70,6 +70,41 @@ __device__ __forceinline__ void store_group(char* base, int64_t e0, int64_t n, u
   }
 }
 
+// Output words of the group whose first element e0 lies kPar elements into
+// unit kb, from the staged words of units [k_lo, k_hi] (unit k_lo at word
+// wphase); every slot index is known at compile time, so the group stays in
+// registers.  Units outside [k_lo, k_hi] hold only elements outside [0, n).
+template <int V, int kPar>
+__device__ __forceinline__ uint4 assemble_group(const uint32_t* swords, int64_t kb, int64_t k_lo,
+                                                int64_t k_hi, uint32_t wphase,
+                                                const TransformParams& t) {
+  using I = VInfo<V>;
+  constexpr int kEpg = 16 / I::es;
+  constexpr int kWpu = I::wpu, kEpu = I::epu, kOwpe = I::ow_per_elem;
+  constexpr int kUnits = (kPar + kEpg - 1) / kEpu + 1;
+  uint32_t gout[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int j = 0; j < kUnits; ++j) {
+    const int64_t k = kb + j;
+    if (k < k_lo || k > k_hi) continue;
+    const int rel = (int)wphase + (int)(k - k_lo) * kWpu;
+    uint32_t w[kWpu];
+#pragma unroll
+    for (int q = 0; q < kWpu; ++q) w[q] = swords[rel + q];
+    uint32_t o[kWpu];
+    unit_outputs<V>(w, o, t);
+#pragma unroll
+    for (int sl = 0; sl < kEpu; ++sl) {
+      const int slot = j * kEpu + sl - kPar;
+      if (slot >= 0 && slot < kEpg) {
+#pragma unroll
+        for (int q = 0; q < kOwpe; ++q) gout[slot * kOwpe + q] = o[sl * kOwpe + q];
+      }
+    }
+  }
+  return make_uint4(gout[0], gout[1], gout[2], gout[3]);
+}
+
 // The groups [g0, g0 + kThreads ipt) of one request (the whole CTA works on
 // one tile, so every branch below is uniform across it).  Group 0 starts
 // head elements (pw = head es / 4 words) before the output; when off - pw is
@@ -82,7 +117,7 @@ __device__ __forceinline__ void batch_tile(const BatchReq& r, uint64_t off_lo, u
                                            int64_t g0, int ipt, uint4* sblocks) {
   using I = VInfo<V>;
   constexpr int kEpg = 16 / I::es;
-  constexpr int kWpu = I::wpu, kEpu = I::epu, kOwpe = I::ow_per_elem;
+  constexpr int kWpu = I::wpu, kEpu = I::epu;
   const int64_t n = r.n, groups = r.groups, head = r.head;
   const uint32_t k0 = r.key0, k1 = r.key1;
   char* base = reinterpret_cast<char*>(r.out);
@@ -122,28 +157,18 @@ __device__ __forceinline__ void batch_tile(const BatchReq& r, uint64_t off_lo, u
     }
     __syncthreads();
     const int64_t e0 = te0 + (int64_t)threadIdx.x * kEpg;
-    const int64_t ge_lo = e0 < 0 ? 0 : e0;
-    const int64_t ge_hi = (e0 + kEpg) < n ? (e0 + kEpg) : n;
-    if (ge_lo < ge_hi) {
-      uint32_t gout[4] = {0u, 0u, 0u, 0u};
-      const int64_t ku_lo = ge_lo / kEpu, ku_hi = (ge_hi - 1) / kEpu;
-      for (int64_t k = ku_lo; k <= ku_hi; ++k) {
-        const int rel = (int)wphase + (int)(k - k_lo) * kWpu;
-        uint32_t w[kWpu];
-#pragma unroll
-        for (int q = 0; q < kWpu; ++q) w[q] = swords[rel + q];
-        uint32_t o[kWpu];
-        unit_outputs<V>(w, o, t);
-#pragma unroll
-        for (int sl = 0; sl < kEpu; ++sl) {
-          const int64_t e = k * kEpu + sl;
-          if (e >= e0 && e < e0 + kEpg) {
-#pragma unroll
-            for (int q = 0; q < kOwpe; ++q) gout[(int)(e - e0) * kOwpe + q] = o[sl * kOwpe + q];
-          }
-        }
+    if (e0 + kEpg > 0 && e0 < n) {
+      uint4 o;
+      if constexpr (kEpu == 1) {
+        o = assemble_group<V, 0>(swords, e0, k_lo, k_hi, wphase, t);
+      } else {
+        // the parity of e0 is the same for every thread (kEpg is even)
+        const int par = (int)(e0 & 1);
+        const int64_t kb = (e0 - par) >> 1;
+        o = par ? assemble_group<V, 1>(swords, kb, k_lo, k_hi, wphase, t)
+                : assemble_group<V, 0>(swords, kb, k_lo, k_hi, wphase, t);
       }
-      store_group<V>(base, e0, n, make_uint4(gout[0], gout[1], gout[2], gout[3]));
+      store_group<V>(base, e0, n, o);
     }
     __syncthreads();
   }
