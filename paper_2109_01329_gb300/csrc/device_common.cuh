@@ -94,7 +94,7 @@ __device__ __forceinline__ double u01_f64(uint32_t wa, uint32_t wb) {
   const uint32_t h = wa >> 11;
   const uint32_t l = __funnelshift_r(wb, wa, 11);  // low 32 bits of x
   if (h == 0) return scaled_u54_to_f64((uint64_t)l, -53);
-  const uint32_t s = (uint32_t)__clz(h) - 11u;     // 0..20
+  const uint32_t s = 20u - (uint32_t)bm64::ilog2_small(h);  // clz(h) - 11, 0..20 (h < 2^21)
   const uint32_t mh = __funnelshift_l(l, h, s);    // high half of x << s
   const uint32_t ml = l << s;
   return __hiloint2double((int)(mh + ((1021u - s) << 20)), (int)ml);
