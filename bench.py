@@ -211,8 +211,8 @@ BM64_PRODUCTS_PER_PAIR = 42
 # current kernels: one launch of 2.68e8 samples scaled by 1e9 / 2.68e8
 # (profiles/gaussian_f64_2.68e8_full.md); replaced when a kernel changes.
 NCU_TRAFFIC_PER_1E9 = {
-    "mrg32k3a/gaussian_f64": (2.083704e9 + 1.169e6) / 0.268,
-    "philox4x32_10/gaussian_f64": (2.083143e9 + 0.298e6) / 0.268,
+    "mrg32k3a/gaussian_f64": (2.083283e9 + 0.076e6) / 0.268,
+    "philox4x32_10/gaussian_f64": (2.082945e9 + 0.298e6) / 0.268,
 }
 PRODUCTS_PER_SAMPLE = {
     "philox4x32_10/bits_u32": 5, "philox4x32_10/uniform_f32": 5,
@@ -330,22 +330,31 @@ def run_serving(grng, torch, dev, seconds, stress):
                        "3 stream slots",
            "events": len(reqs), "samples": int(4 * hits.sum())}
     srv = grng.Server(4 << 30, num_streams=3, auto_release=True, device=dev)
-    for name, scale in (("real_time", 1.0), (f"stress_{stress:g}x", 1.0 / stress),
-                        ("burst", 1e-9)):
-        srv.reset_stats()
-        srv.replay(t, reqs, time_scale=scale)
-        srv.drain(timeout_s=600)
-        st = srv.stats()
-        out[name] = {"gsamples_s": round(st["samples"] / st["wall_s"] / 1e9, 3) if st["wall_s"]
-                     else None,
-                     "latency_p50_us": round(st["latency_p50_us"], 1),
-                     "latency_p99_us": round(st["latency_p99_us"], 1),
-                     "latency_max_us": round(st["latency_max_us"], 1),
-                     "completed": st["completed"], "rejected": st["rejected"],
-                     "batches": st["batches"],
-                     "mean_batch_events": round(st["mean_batch_requests"], 2),
-                     "peak_pool_gb": round(st["peak_pool_bytes"] / 1e9, 3),
-                     "wall_s": round(st["wall_s"], 3)}
+    # the burst (every event at once) lasts a few tens of milliseconds, so it is
+    # replayed five times and the median run is reported
+    for name, scale, runs in (("real_time", 1.0, 1), (f"stress_{stress:g}x", 1.0 / stress, 1),
+                              ("burst", 1e-9, 5)):
+        results = []
+        for _ in range(runs):
+            srv.reset_stats()
+            srv.replay(t, reqs, time_scale=scale)
+            srv.drain(timeout_s=600)
+            st = srv.stats()
+            results.append({
+                "gsamples_s": round(st["samples"] / st["wall_s"] / 1e9, 3) if st["wall_s"]
+                else None,
+                "latency_p50_us": round(st["latency_p50_us"], 1),
+                "latency_p99_us": round(st["latency_p99_us"], 1),
+                "latency_max_us": round(st["latency_max_us"], 1),
+                "completed": st["completed"], "rejected": st["rejected"],
+                "batches": st["batches"],
+                "mean_batch_events": round(st["mean_batch_requests"], 2),
+                "peak_pool_gb": round(st["peak_pool_bytes"] / 1e9, 3),
+                "wall_s": round(st["wall_s"], 3)})
+        results.sort(key=lambda r: r["gsamples_s"] or 0.0)
+        out[name] = dict(results[len(results) // 2])
+        if runs > 1:
+            out[name]["runs_gsamples_s"] = [r["gsamples_s"] for r in results]
     srv.close()
     # the plain form: two grng_generate launches per event, back to back on one
     # stream, into one preallocated buffer (no admission, no batching)
@@ -585,12 +594,16 @@ def run_ours(args):
         host = torch.empty(n * 8, dtype=torch.uint8, pin_memory=True)
         work = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+        case_ms = {}
+
         def e2e_step():
             for ek, en, (name, kind, dtype, p0, p1) in cases:
                 es = 8 if dtype == 2 else 4
                 e = grng.Engine(ek, W.SWEEP_SEED, rank_offset(kind, dtype))
+                tc = time.perf_counter()
                 grng.generate_host(grng.Distribution(kind, dtype, p0, p1), e,
                                    host[: n * es].view(tdt[dtype]), work)
+                case_ms[f"{en}/{name}"] = round((time.perf_counter() - tc) * 1e3, 2)
 
         e2e_step()
         if world > 1:
@@ -620,7 +633,7 @@ def run_ours(args):
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
                "ms_per_step": dt / args.e2e_steps * 1e3,
                "d2h_gbs": round(e2e_gbs, 1), "link_gbs": round(link_gbs, 1),
-               "frac_link": round(e2e_gbs / link_gbs, 4),
+               "frac_link": round(e2e_gbs / link_gbs, 4), "per_case_ms": case_ms,
                "how": "grng_generate_host into pinned host memory, 256 MiB device staging, "
                       "host wall clock; link_gbs is a plain 2 GiB device-to-pinned-host copy"}
         del host, work
