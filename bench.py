@@ -251,6 +251,41 @@ def _pct(xs, q):
     return xs[min(len(xs) - 1, int(round(q / 100.0 * (len(xs) - 1))))]
 
 
+# Fills outside the config-2 sweep, timed the same way: the inverse-CDF methods,
+# FP64 lognormal, the affine FP64 gaussian and a general FP32 range.
+EXTRA_DISTS = [
+    ("icdf_gaussian_f32", 4, 1, 0.0, 1.0), ("icdf_lognormal_f32", 5, 1, 0.0, 1.0),
+    ("icdf_gaussian_f64", 4, 2, 0.0, 1.0), ("lognormal_f64", 3, 2, 0.0, 1.0),
+    ("gaussian_f64_m3_s0.25", 2, 2, -3.0, 0.25), ("uniform_f32_2_5", 1, 1, 2.0, 5.0),
+]
+
+
+def run_extra(grng, torch, dev, n, buf, stream, reps, hbm_peak):
+    out = {}
+    tdt = {0: torch.int32, 1: torch.float32, 2: torch.float64}
+    for ek, en in ENGINES:
+        for name, kind, dtype, p0, p1 in EXTRA_DISTS:
+            es = 8 if dtype == 2 else 4
+            view = buf[: n * es].view(tdt[dtype])
+            d = grng.Distribution(kind, dtype, p0, p1)
+            e = grng.Engine(ek, W.SWEEP_SEED, 0)
+            with torch.cuda.stream(stream):
+                grng.generate(d, e, view, stream=stream)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(reps)]
+                for a, b in ev:
+                    a.record(stream)
+                    grng.generate(d, e, view, stream=stream)
+                    b.record(stream)
+            torch.cuda.synchronize()
+            ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+            gbs = n * es / (ms * 1e-3) / 1e9
+            out[f"{en}/{name}"] = {"ms": round(ms, 4), "gsamples_s": round(n / ms / 1e6, 2),
+                                   "write_gbs": round(gbs, 1),
+                                   "frac_hbm": round(gbs / hbm_peak, 4)}
+    return out
+
+
 def run_batched(grng, torch, dev, reps):
     """Config 4: 4096 Philox engines (seeds 1..4096), log-uniform sizes in
     [64, 2^20], five distributions; one graph-replayed persistent launch vs
@@ -638,6 +673,10 @@ def run_ours(args):
                       "host wall clock; link_gbs is a plain 2 GiB device-to-pinned-host copy"}
         del host, work
 
+    extra = None
+    if rank == 0 and not args.skip_extra:
+        extra = run_extra(grng, torch, dev, n, buf, stream, 3, hbm_peak)
+
     batched = None
     if rank == 0 and not args.skip_batched:
         batched = run_batched(grng, torch, dev, args.batch_reps)
@@ -677,7 +716,8 @@ def run_ours(args):
                                           "gsamples_s": target["gsamples_s"]},
             "ceilings": {"hbm_copy_gbs": hbm_peak, "write_only_gbs": round(write_gbs, 1),
                          "products_per_s": mul_rate, "products_per_s_probe": mul_probe},
-            "per_kernel": per_kernel, "curand": curand, "batched": batched, "serving": serving,
+            "per_kernel": per_kernel, "curand": curand, "other_fills": extra,
+            "batched": batched, "serving": serving,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": args.steps * len(cases)}
     if rank == 0:
@@ -703,6 +743,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="skip the fills outside the sweep (inverse CDF, FP64 lognormal, ...)")
     ap.add_argument("--batch-reps", type=int, default=20)
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="seconds of the arrival trace to replay in real time (0: skip)")

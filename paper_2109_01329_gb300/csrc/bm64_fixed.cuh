@@ -52,12 +52,14 @@ __device__ const uint64_t d_logt[GRNG_BM64_LOGT_LEN] = GRNG_BM64_LOGT;
 __device__ const uint64_t d_sint[GRNG_BM64_SINT_LEN] = GRNG_BM64_SINT;
 __device__ const uint64_t d_cost[GRNG_BM64_COST_LEN] = GRNG_BM64_COST;
 __device__ const uint64_t d_e58[GRNG_BM64_E58_LEN] = GRNG_BM64_E58;
+__device__ const uint64_t d_exp2t[GRNG_BM64_EXP2T_LEN] = GRNG_BM64_EXP2T;
 #endif
 static const uint32_t h_logc[GRNG_BM64_LOGC_LEN] = GRNG_BM64_LOGC;
 static const uint64_t h_logt[GRNG_BM64_LOGT_LEN] = GRNG_BM64_LOGT;
 static const uint64_t h_sint[GRNG_BM64_SINT_LEN] = GRNG_BM64_SINT;
 static const uint64_t h_cost[GRNG_BM64_COST_LEN] = GRNG_BM64_COST;
 static const uint64_t h_e58[GRNG_BM64_E58_LEN] = GRNG_BM64_E58;
+static const uint64_t h_exp2t[GRNG_BM64_EXP2T_LEN] = GRNG_BM64_EXP2T;
 
 #if defined(__CUDA_ARCH__)
 #define GRNG_BM_TABLE(d, h, i) __ldg(&d[i])
@@ -69,6 +71,7 @@ GRNG_BM_HD uint64_t logt(uint32_t i) { return GRNG_BM_TABLE(d_logt, h_logt, i); 
 GRNG_BM_HD uint64_t sint(uint32_t j) { return GRNG_BM_TABLE(d_sint, h_sint, j); }
 GRNG_BM_HD uint64_t cost(uint32_t j) { return GRNG_BM_TABLE(d_cost, h_cost, j); }
 GRNG_BM_HD uint64_t e58(uint32_t e) { return GRNG_BM_TABLE(d_e58, h_e58, e); }
+GRNG_BM_HD uint64_t exp2t(uint32_t j) { return GRNG_BM_TABLE(d_exp2t, h_exp2t, j); }
 #undef GRNG_BM_TABLE
 
 // 32 x 32 -> 64-bit product, and its high word.
@@ -350,25 +353,127 @@ GRNG_BM_HD double assemble(uint64_t p, int k, bool neg) {
   return d;
 }
 
+// The Box-Muller pair in fixed point: z0 = (n0 ? -p0 : p0) 2^k,
+// z1 = (n1 ? -p1 : p1) 2^k, p0, p1 < 2^62; u1 = 1 gives p0 = p1 = 0.
+struct FixedPair {
+  uint64_t p0, p1;
+  int k;
+  bool n0, n1;
+};
+
 // The Box-Muller pair for 53-bit x1 (u1 = (x1 + 1) 2^-53) and x2 (u2 = x2 2^-53).
-GRNG_BM_HD void box_muller(uint64_t x1, uint64_t x2, double& z0, double& z1) {
+GRNG_BM_HD FixedPair box_muller_fixed(uint64_t x1, uint64_t x2) {
   const uint64_t m1 = x1 + 1u;
   uint64_t c_abs, s_abs;
   bool c_neg, s_neg;
   sincos_turns(x2, c_abs, c_neg, s_abs, s_neg);
+  FixedPair r;
+  r.n0 = c_neg;
+  r.n1 = s_neg;
   if (m1 >> 53) {  // u1 = 1: rho = 0
-    z0 = 0.0;
-    z1 = 0.0;
-    return;
+    r.p0 = r.p1 = 0;
+    r.k = 0;
+    return r;
   }
   uint64_t lm, sq;
   int le, se;
   neg_log(m1, lm, le);
   sqrt2x(lm, le, sq, se);
   // z = sq 2^se * c 2^-63 = umulhi(sq, c) 2^(se + 1)
-  z0 = assemble(umulhi_apx(sq, c_abs), se + 1, c_neg);
-  z1 = assemble(umulhi_apx(sq, s_abs), se + 1, s_neg);
+  r.p0 = umulhi_apx(sq, c_abs);
+  r.p1 = umulhi_apx(sq, s_abs);
+  r.k = se + 1;
+  return r;
 }
+
+GRNG_BM_HD void box_muller(uint64_t x1, uint64_t x2, double& z0, double& z1) {
+  const FixedPair f = box_muller_fixed(x1, x2);
+  z0 = assemble(f.p0, f.k, f.n0);
+  z1 = assemble(f.p1, f.k, f.n1);
+}
+
+// exp(m + s z) for z = (neg ? -p : p) 2^k, written exp(m) 2^(s z log2 e):
+// exp(m) = em_mant 2^em_exp (em_mant normalised) and s = s_mant 2^s_exp
+// (s_mant the 53-bit significand) are prepared per launch on the host.
+// V = s z log2 e splits into n + f, f in [0, 1); 2^f = 2^(j/256) e^t with a
+// 257-entry table and t = (f - j/256) ln 2 < 2^-8.5, e^t - 1 summed to t^5
+// (t^6/720 < 2^-60; t^3..t^5 from 32-bit high products of t 2^40).  Returns
+// false, leaving the output to the caller's FP64 path, when |V| >= 2^11 or
+// the result is not a normal double.  Error: below 2^-51 relative besides
+// the error of z itself, which s z log2 e carries into the exponent.
+GRNG_BM_HD bool lognormal_fixed(uint64_t p, int k, bool neg, uint64_t em_mant, int em_exp,
+                                uint64_t s_mant, int s_exp, double& out) {
+  const uint64_t W = umulhi_apx(s_mant << 11, p);          // |s z| = W 2^(k + s_exp + 53)
+  const uint64_t W2 = umulhi_apx(W, kLog2e63);             // |V| = W2 2^(k + s_exp + 54)
+  const int sh = k + s_exp + 54 + 52;                      // A = |V| 2^52 = W2 2^sh
+  uint64_t A;
+  if (sh >= 0) {
+    if (sh >= 63 || (W2 >> (63 - sh)) != 0) return false;   // |V| >= 2^11
+    A = W2 << sh;
+  } else {
+    A = sh <= -64 ? 0ull : (W2 >> (-sh));
+  }
+  // V = n + f with f = F 2^-52 in [0, 1)
+  const int nabs = (int)(A >> 52);
+  uint64_t F = A & ((1ull << 52) - 1);
+  int n = nabs;
+  if (neg && A != 0) {
+    if (F != 0) {
+      n = -nabs - 1;
+      F = (1ull << 52) - F;
+    } else {
+      n = -nabs;
+    }
+  }
+  const uint32_t j = (uint32_t)(F >> 44);
+  const uint64_t G = F & ((1ull << 44) - 1);               // (f - j/256) 2^52
+  const uint64_t T = umulhi_apx(G << 20, kLn2) >> 8;       // t 2^64 < 2^55.5
+  const uint32_t t40 = (uint32_t)(T >> 24);                // t 2^40
+  const uint32_t q = mulh(t40, t40);                       // t^2 2^48
+  const uint32_t c = mulh(q, t40);                         // t^3 2^56
+  const uint32_t d = mulh(q, q);                           // t^4 2^64
+  const uint32_t e5 = mulh(d, t40);                        // t^5 2^72
+  const uint64_t Ex = T + (sqr_hi(T) >> 1) + (mulw(c, 0x2AAAAAABu) >> 24) +  // t + t^2/2 + t^3/6
+                      mulh(d, 0x0AAAAAABu) + (mulh(e5, 0x02222222u) >> 8);  // + t^4/24 + t^5/120
+  const uint64_t P = exp2t(j);                             // 2^(j/256) 2^62
+  const uint64_t M = P + umulhi_apx(P, Ex);                // 2^f 2^62 in [2^62, 2^63]
+  const uint64_t R = umulhi_apx(em_mant, M);               // exp(m) 2^f = R 2^(em_exp + 2)
+  const int kk = em_exp + 2 + n;                           // R in [2^61, 2^63)
+  if (kk + 62 > 1023 || kk + 61 < -1022) return false;
+  out = assemble(R, kk, false);
+  return true;
+}
+
+#if !defined(__CUDA_ARCH__)
+// Host side of lognormal_fixed: exp(m) and s split for a launch; false when
+// the fixed-point path is not used: |m| > 11000 (every output is then 0 or
+// infinite) or s outside [2^-60, 2^20].  exp(m) keeps an integer exponent,
+// so m + s z may lie anywhere in the double range.
+inline bool lognormal_consts(double m, double s, uint64_t& em_mant, int& em_exp,
+                             uint64_t& s_mant, int& s_exp) {
+  if (!(std::fabs(m) <= 11000.0) || !(s >= 0x1p-60) || !(s <= 0x1p20)) return false;
+  int ex = 0;
+  const long double fr = std::frexp(std::exp((long double)m), &ex);  // [1/2, 1)
+  const long double scaled = std::ldexp(fr, 64);                      // [2^63, 2^64)
+  long double hi = std::floor(scaled);
+  uint64_t mant = (uint64_t)hi;
+  if (scaled - hi >= 0.5L) {
+    if (mant == ~0ull) {
+      mant = 1ull << 63;
+      ex += 1;
+    } else {
+      mant += 1;
+    }
+  }
+  em_mant = mant;
+  em_exp = ex - 64;
+  int es = 0;
+  const double fs = std::frexp(s, &es);                               // [1/2, 1)
+  s_mant = (uint64_t)std::ldexp(fs, 53);
+  s_exp = es - 53;
+  return true;
+}
+#endif
 
 }  // namespace bm64
 }  // namespace grng

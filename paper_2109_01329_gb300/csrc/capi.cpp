@@ -16,6 +16,7 @@
 
 #include "grng.h"
 #include "grng_internal.h"
+#include "bm64_fixed.cuh"
 #include "mrg_tables.h"
 
 struct grng_engine {
@@ -230,7 +231,16 @@ int choose_variant(const grng_distribution* d, TransformParams* t) {
       }
       t->dmean = d->p0;
       t->dsd = d->p1;
-      if (logn) return V_LOGN_F64;
+      if (logn) {
+        uint64_t em = 0, sm = 0;
+        int ee = 0, se = 0;
+        t->ln_fast = bm64::lognormal_consts(d->p0, d->p1, em, ee, sm, se) ? 1 : 0;
+        t->ln_em_mant = em;
+        t->ln_em_exp = ee;
+        t->ln_s_mant = sm;
+        t->ln_s_exp = se;
+        return V_LOGN_F64;
+      }
       // fma(1, z, 0) == z, so (0, 1) drops the affine step exactly
       return (d->p0 == 0.0 && d->p1 == 1.0) ? V_STDGAUSS_F64 : V_GAUSS_F64;
     }

@@ -239,7 +239,24 @@ __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
     const uint64_t b = (uint64_t)__double_as_longlong(y);
     o[0] = (uint32_t)b;
     o[1] = (uint32_t)(b >> 32);
-  } else {  // V_GAUSS_F64, V_LOGN_F64, V_STDGAUSS_F64
+  } else if constexpr (V == V_LOGN_F64) {
+    // exp(m + s z) in fixed point from the fixed-point pair (no FP64
+    // instruction); an output outside its range takes the FP64 path
+    const bm64::FixedPair f = bm64::box_muller_fixed(u53(w[0], w[1]), u53(w[2], w[3]));
+    double y0, y1;
+    if (!(t.ln_fast && bm64::lognormal_fixed(f.p0, f.k, f.n0, t.ln_em_mant, t.ln_em_exp,
+                                             t.ln_s_mant, t.ln_s_exp, y0)))
+      y0 = exp(fma(t.dsd, bm64::assemble(f.p0, f.k, f.n0), t.dmean));
+    if (!(t.ln_fast && bm64::lognormal_fixed(f.p1, f.k, f.n1, t.ln_em_mant, t.ln_em_exp,
+                                             t.ln_s_mant, t.ln_s_exp, y1)))
+      y1 = exp(fma(t.dsd, bm64::assemble(f.p1, f.k, f.n1), t.dmean));
+    const uint64_t b0 = (uint64_t)__double_as_longlong(y0);
+    const uint64_t b1 = (uint64_t)__double_as_longlong(y1);
+    o[0] = (uint32_t)b0;
+    o[1] = (uint32_t)(b0 >> 32);
+    o[2] = (uint32_t)b1;
+    o[3] = (uint32_t)(b1 >> 32);
+  } else {  // V_GAUSS_F64, V_STDGAUSS_F64
     double z0, z1;
     box_muller_f64(w[0], w[1], w[2], w[3], z0, z1);
     double y0 = z0, y1 = z1;
@@ -249,10 +266,6 @@ __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
     if constexpr (V != V_STDGAUSS_F64) {
       y0 = fma(t.dsd, z0, t.dmean);
       y1 = fma(t.dsd, z1, t.dmean);
-    }
-    if constexpr (V == V_LOGN_F64) {
-      y0 = exp(y0);
-      y1 = exp(y1);
     }
     const uint64_t b0 = (uint64_t)__double_as_longlong(y0);
     const uint64_t b1 = (uint64_t)__double_as_longlong(y1);

@@ -9,9 +9,11 @@ Tables (emitted as initializer macros GRNG_BM64_LOGC, _LOGT, _SINT, _COST)
   kLogT[i]:              ln(c_i) * 2^64 (c_i exactly as stored)
   kSinT[j], kCosT[j], j = 0..1024:  sin, cos(2 pi j / 8192) * 2^63
   kE58[e], e = 0..52:    e ln 2 * 2^58
+  kExp2T[j], j = 0..256: 2^(j / 256) * 2^62
 Scalars
   kLn2:    ln 2 * 2^64
   k2Pi61:  2 pi * 2^61
+  kLog2e63: log2(e) * 2^63,  kLn2_64 is kLn2
   kInv2 .. kInv7: 2^64 / k (truncated)
   kInv4_32 .. kInv7_32: 2^32 / k (truncated)
   kInv24_32, kInv120_32, kInv720_32: 2^64 / 6 and 2^32 / {24, 120, 720}
@@ -47,9 +49,12 @@ def main():
     cost = [rnd(mp.cos(2 * mp.pi * j / 8192) * two63) for j in range(1025)]
     e58 = [rnd(e * mp.log(2) * mp.mpf(2) ** 58) for e in range(53)]
     assert all(v < 1 << 64 for v in e58)
+    exp2t = [rnd(mp.mpf(2) ** (mp.mpf(j) / 256) * mp.mpf(2) ** 62) for j in range(257)]
+    assert exp2t[0] == 1 << 62 and exp2t[256] == 1 << 63
 
     out.append(f"constexpr uint64_t kLn2 = {rnd(mp.log(2) * two64)}ull;")
     out.append(f"constexpr uint64_t k2Pi61 = {rnd(2 * mp.pi * mp.mpf(2) ** 61)}ull;")
+    out.append(f"constexpr uint64_t kLog2e63 = {rnd(mp.log(mp.e, 2) * mp.mpf(2) ** 63)}ull;")
     for k in range(2, 8):
         out.append(f"constexpr uint64_t kInv{k} = {(1 << 64) // k}ull;")
     out.append(f"constexpr uint32_t kInv24_32 = {rnd(mp.mpf(2) ** 32 / 24)}u;")
@@ -60,7 +65,7 @@ def main():
     # table bodies as macros: the device and host copies are declared where used
     for name, ctype, vals in [("LOGC", "uint32_t", logc), ("LOGT", "uint64_t", logt),
                               ("SINT", "uint64_t", sint), ("COST", "uint64_t", cost),
-                              ("E58", "uint64_t", e58)]:
+                              ("E58", "uint64_t", e58), ("EXP2T", "uint64_t", exp2t)]:
         suffix = "ull" if "64" in ctype else "u"
         out.append(f"#define GRNG_BM64_{name}_LEN {len(vals)}")
         out.append(f"#define GRNG_BM64_{name} {{ \\")

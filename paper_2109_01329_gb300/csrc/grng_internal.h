@@ -58,6 +58,11 @@ struct TransformParams {
   double dmean, dsd;          // F64 gaussian / lognormal
   int64_t aff_a;              // F64 exact affine: r = (aff_a + x) 2^aff_exp, x = 53-bit word
   int32_t aff_exp;
+  // F64 lognormal in fixed point: exp(m) = ln_em_mant 2^ln_em_exp, s = ln_s_mant 2^ln_s_exp;
+  // ln_fast = 0 keeps every output on the FP64 path
+  int32_t ln_fast;
+  uint64_t ln_em_mant, ln_s_mant;
+  int32_t ln_em_exp, ln_s_exp;
 };
 
 // One fill request as the launchers see it: num_streams streams of n

@@ -119,6 +119,21 @@ def test_fp64_box_muller_edges(g, kind, p0, p1):
     _check(kind, 2, got, ref, f"FP64 kind {kind} ({p0}, {p1})")
 
 
+@pytest.mark.parametrize("m,s", [(0.0, 1.0), (-3.0, 2.0), (650.0, 1.0), (701.0, 0.5),
+                                 (-705.0, 2.0), (1.0, 20.0), (1.0, 2.0**-61)])
+def test_fp64_lognormal_ranges(g, m, s):
+    """The fixed-point lognormal exp(m) 2^(s z log2 e) and its FP64 fallbacks:
+    s below 2^-60 sends the whole launch to FP64, outputs below the normal
+    range (m = -705) take it one by one; the rest stays in fixed point, also
+    where m + s z rounded to a double would lose more than 1e-14 (m = 701)."""
+    w = _fp64_edge_pairs(seed=4, n_random=30000)
+    n = w.size // 2
+    got = _gpu(g, 3, 2, m, s, w, n)
+    ref = oracle.transform_words(3, 2, m, s, n, w)
+    assert np.all(np.isfinite(got)) and np.all(got >= 0)
+    _check(3, 2, got, ref, f"FP64 lognormal ({m}, {s})")
+
+
 def test_fp64_uniform_edges(g):
     w = _fp64_edge_pairs(seed=2, n_random=50000)
     n = w.size // 2
