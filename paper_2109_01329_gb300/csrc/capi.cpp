@@ -254,6 +254,15 @@ int choose_variant(const grng_distribution* d, TransformParams* t) {
       }
       t->dmean = d->p0;
       t->dsd = d->p1;
+      if (logn) {
+        uint64_t em = 0, sm = 0;
+        int ee = 0, se = 0;
+        t->ln_fast = bm64::lognormal_consts(d->p0, d->p1, em, ee, sm, se) ? 1 : 0;
+        t->ln_em_mant = em;
+        t->ln_em_exp = ee;
+        t->ln_s_mant = sm;
+        t->ln_s_exp = se;
+      }
       return logn ? V_ICDF_LOGN_F64 : V_ICDF_GAUSS_F64;
     }
     default: return -1;

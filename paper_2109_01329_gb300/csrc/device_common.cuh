@@ -7,6 +7,7 @@
 
 #include "bm64_fixed.cuh"
 #include "grng_internal.h"
+#include "icdf64_fixed.cuh"
 
 namespace grng {
 namespace dev {
@@ -231,11 +232,20 @@ __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
     if constexpr (V == V_ICDF_LOGN_F32) y = expf(y);
     o[0] = __float_as_uint(y);
   } else if constexpr (V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64) {
-    // u = (x + 1/2) 2^-52, x = ((w_a << 32) | w_b) >> 12
+    // u = (x + 1/2) 2^-52, x = ((w_a << 32) | w_b) >> 12; Phi^-1 in fixed
+    // point (icdf64_fixed.cuh), then mean + sd z or exp(m + s z) as for the
+    // Box-Muller outputs
     const uint64_t x = ((((uint64_t)w[0]) << 32) | (uint64_t)w[1]) >> 12;
-    const double u = scaled_u54_to_f64(2u * x + 1u, -53);
-    double y = fma(t.dsd, normcdfinv(u), t.dmean);
-    if constexpr (V == V_ICDF_LOGN_F64) y = exp(y);
+    bool neg;
+    const uint64_t t59 = icdf64::icdf_t59(x, neg);
+    double y;
+    if constexpr (V == V_ICDF_GAUSS_F64) {
+      y = fma(t.dsd, bm64::assemble(t59, -59, neg), t.dmean);
+    } else {
+      if (!(t.ln_fast && bm64::lognormal_fixed(t59, -59, neg, t.ln_em_mant, t.ln_em_exp,
+                                               t.ln_s_mant, t.ln_s_exp, y)))
+        y = exp(fma(t.dsd, bm64::assemble(t59, -59, neg), t.dmean));
+    }
     const uint64_t b = (uint64_t)__double_as_longlong(y);
     o[0] = (uint32_t)b;
     o[1] = (uint32_t)(b >> 32);
@@ -310,8 +320,8 @@ struct VInfo {
                                  : 1;
   static constexpr int ow_per_elem = es / 4;  // output words per element
   // instruction weight of one unit: 0 a few operations, 1 a single-precision
-  // log / sincos / inverse CDF, 2 the fixed-point FP64 Box-Muller or a
-  // double-precision inverse CDF / exp (hundreds of instructions); loops
+  // log / sincos / inverse CDF, 2 the fixed-point FP64 Box-Muller, inverse
+  // CDF or lognormal (hundreds of instructions); loops
   // over units unroll less as the weight grows, so a loop body stays in the
   // instruction cache
   static constexpr int weight =

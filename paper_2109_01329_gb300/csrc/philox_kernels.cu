@@ -113,7 +113,7 @@ __device__ __forceinline__ void philox_stream_body(const StreamParams& p) {
 template <int V>
 constexpr bool stream_wants_5_ctas() {
   return V == V_GAUSS_F32 || V == V_LOGN_F32 || V == V_ICDF_GAUSS_F32 || V == V_GAUSS_F64 ||
-         V == V_STDGAUSS_F64 || V == V_LOGN_F64;
+         V == V_STDGAUSS_F64 || V == V_LOGN_F64 || V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64;
 }
 
 template <int V, int U, bool kHiUniform>
@@ -318,8 +318,10 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.jf = jf;
     p.jl = jl;
     constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 4
-                       : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64) ? 1
-                                                                         : 2;
+                       : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64 ||
+                          V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64)
+                           ? 1
+                           : 2;
     const bool hi_uniform = base_lo + (uint64_t)groups >= base_lo;  // no carry into the top half
     void (*kernel)(const StreamParams);
     if constexpr (stream_wants_5_ctas<V>()) {
