@@ -46,18 +46,19 @@
 namespace grng {
 namespace bm64 {
 
+// (sin, cos) and (ln c_i, c_i) are interleaved so that each lookup is one
+// 16-byte load.
+struct U64Pair {
+  uint64_t a, b;
+};
 #if defined(__CUDACC__)
-__device__ const uint32_t d_logc[GRNG_BM64_LOGC_LEN] = GRNG_BM64_LOGC;
-__device__ const uint64_t d_logt[GRNG_BM64_LOGT_LEN] = GRNG_BM64_LOGT;
-__device__ const uint64_t d_sint[GRNG_BM64_SINT_LEN] = GRNG_BM64_SINT;
-__device__ const uint64_t d_cost[GRNG_BM64_COST_LEN] = GRNG_BM64_COST;
+__device__ const ulonglong2 d_sc[GRNG_BM64_SINT_LEN] = GRNG_BM64_SC;
+__device__ const ulonglong2 d_lt[GRNG_BM64_LOGT_LEN] = GRNG_BM64_LT;
 __device__ const uint64_t d_e58[GRNG_BM64_E58_LEN] = GRNG_BM64_E58;
 __device__ const uint64_t d_exp2t[GRNG_BM64_EXP2T_LEN] = GRNG_BM64_EXP2T;
 #endif
-static const uint32_t h_logc[GRNG_BM64_LOGC_LEN] = GRNG_BM64_LOGC;
-static const uint64_t h_logt[GRNG_BM64_LOGT_LEN] = GRNG_BM64_LOGT;
-static const uint64_t h_sint[GRNG_BM64_SINT_LEN] = GRNG_BM64_SINT;
-static const uint64_t h_cost[GRNG_BM64_COST_LEN] = GRNG_BM64_COST;
+static const U64Pair h_sc[GRNG_BM64_SINT_LEN] = GRNG_BM64_SC;
+static const U64Pair h_lt[GRNG_BM64_LOGT_LEN] = GRNG_BM64_LT;
 static const uint64_t h_e58[GRNG_BM64_E58_LEN] = GRNG_BM64_E58;
 static const uint64_t h_exp2t[GRNG_BM64_EXP2T_LEN] = GRNG_BM64_EXP2T;
 
@@ -66,13 +67,31 @@ static const uint64_t h_exp2t[GRNG_BM64_EXP2T_LEN] = GRNG_BM64_EXP2T;
 #else
 #define GRNG_BM_TABLE(d, h, i) h[i]
 #endif
-GRNG_BM_HD uint32_t logc(uint32_t i) { return GRNG_BM_TABLE(d_logc, h_logc, i); }
-GRNG_BM_HD uint64_t logt(uint32_t i) { return GRNG_BM_TABLE(d_logt, h_logt, i); }
-GRNG_BM_HD uint64_t sint(uint32_t j) { return GRNG_BM_TABLE(d_sint, h_sint, j); }
-GRNG_BM_HD uint64_t cost(uint32_t j) { return GRNG_BM_TABLE(d_cost, h_cost, j); }
 GRNG_BM_HD uint64_t e58(uint32_t e) { return GRNG_BM_TABLE(d_e58, h_e58, e); }
 GRNG_BM_HD uint64_t exp2t(uint32_t j) { return GRNG_BM_TABLE(d_exp2t, h_exp2t, j); }
 #undef GRNG_BM_TABLE
+// sin and cos of 2 pi j / 8192 (2^63 scale)
+GRNG_BM_HD void sincos_tab(uint32_t j, uint64_t& s, uint64_t& c) {
+#if defined(__CUDA_ARCH__)
+  const ulonglong2 v = __ldg(&d_sc[j]);
+  s = v.x;
+  c = v.y;
+#else
+  s = h_sc[j].a;
+  c = h_sc[j].b;
+#endif
+}
+// ln c_i 2^64 and c_i 2^24
+GRNG_BM_HD void log_tab(uint32_t i, uint64_t& t, uint32_t& c) {
+#if defined(__CUDA_ARCH__)
+  const ulonglong2 v = __ldg(&d_lt[i]);
+  t = v.x;
+  c = (uint32_t)v.y;
+#else
+  t = h_lt[i].a;
+  c = (uint32_t)h_lt[i].b;
+#endif
+}
 
 // 32 x 32 -> 64-bit product, and its high word.
 GRNG_BM_HD uint64_t mulw(uint32_t a, uint32_t b) { return (uint64_t)a * b; }
@@ -215,7 +234,9 @@ GRNG_BM_HD void neg_log(uint64_t m1, uint64_t& lm, int& le) {
     le = -63 - nz - c;
     return;
   }
-  const uint32_t C = logc(i);               // c_i 2^24
+  uint64_t Ti;                              // ln c_i 2^64
+  uint32_t C;                               // c_i 2^24
+  log_tab(i, Ti, C);
   // r 2^64 = 2^64 - M C 2^-24 (truncating M C 2^-24 leaves r >= 0); the
   // 96-bit product M C is exact, and M C 2^-24 = (hi << 8) | (lo32 >> 24)
   uint64_t mc_hi;
@@ -238,7 +259,7 @@ GRNG_BM_HD void neg_log(uint64_t m1, uint64_t& lm, int& le) {
   const uint64_t S = R + (sqr_hi(R) >> 1) + T3 + T456;
   // -ln(1 - delta) 2^64 = ln c_i 2^64 + S < ln 2 2^64 + 2^55; with e >= 1
   // the sum e ln 2 + ... is kept in units of 2^-58 (below 37 2^58 < 2^64)
-  uint64_t Lf = logt(i) + S;
+  uint64_t Lf = Ti + S;
   int lb = -64;
   if (e != 0) {
     Lf = e58(e) + (Lf >> 6);
@@ -311,7 +332,8 @@ GRNG_BM_HD void sincos_turns(uint64_t x2, uint64_t& c_abs, bool& c_neg, uint64_t
   // (C + iS)(1 - eps + i sphi) = C + iS + (C + iS)(-eps + i sphi), the last
   // product as k1 = eps (C + S), k2 = C (sphi + eps), k3 = S (sphi - eps):
   // cos = C - k1 - k3, sin = S + k2 - k1
-  const uint64_t Sj = sint(j), Cj = cost(j);
+  uint64_t Sj, Cj;
+  sincos_tab(j, Sj, Cj);
   const uint64_t k1 = umulhi_apx(Cj + Sj, eps);
   const uint64_t k2 = umulhi_apx(Cj, sphi + eps);
   const uint64_t k3 = umulhi_apx(Sj, sphi - eps);
@@ -334,7 +356,11 @@ GRNG_BM_HD void sincos_turns(uint64_t x2, uint64_t& c_abs, bool& c_neg, uint64_t
 GRNG_BM_HD double assemble(uint64_t p, int k, bool neg) {
   const uint32_t ph = (uint32_t)(p >> 32), pl = (uint32_t)p;
   uint32_t mh, ml, s;
-  if (ph != 0) {
+  if (ph >= 256u) {                                 // clz(ph) from the float exponent
+    s = 23u - (uint32_t)ilog2_small(ph >> 8);
+    mh = shl_hi(pl, ph, s);
+    ml = pl << s;
+  } else if (ph != 0) {                             // p < 2^40 (rare)
     s = clz32(ph);
     mh = shl_hi(pl, ph, s);
     ml = pl << s;

@@ -62,6 +62,12 @@ def main():
         out.append(f"constexpr uint32_t kInv{k}_32 = {(1 << 32) // k}u;")
     out.append(f"constexpr uint32_t kInv120_32 = {rnd(mp.mpf(2) ** 32 / 120)}u;")
     out.append(f"constexpr uint32_t kInv720_32 = {rnd(mp.mpf(2) ** 32 / 720)}u;")
+    # interleaved pairs, one 16-byte load each: (sin, cos) and (ln c_i, c_i)
+    for name, a, b in (("SC", sint, cost), ("LT", logt, logc)):
+        out.append(f"#define GRNG_BM64_{name} {{ \\")
+        for k in range(0, len(a), 2):
+            out.append("    " + ", ".join(f"{{{a[i]}ull, {b[i]}ull}}" for i in range(k, min(k + 2, len(a)))) + ", \\")
+        out.append("}")
     # table bodies as macros: the device and host copies are declared where used
     for name, ctype, vals in [("LOGC", "uint32_t", logc), ("LOGT", "uint64_t", logt),
                               ("SINT", "uint64_t", sint), ("COST", "uint64_t", cost),
