@@ -415,6 +415,17 @@ def run_serving(grng, torch, dev, seconds, stress):
     return out
 
 
+def sweep_config(n: int, world: int) -> dict:
+    """The workload both arms report: the config-2 fill sweep."""
+    return {"workload": f"fill sweep n={n:.0e} per GPU: Philox4x32-10 and MRG32k3a x "
+                        "{bits u32, uniform f32 [0,1), uniform f64 [0,1), gaussian "
+                        "f32 (0,1), gaussian f64 (0,1), lognormal f32 (0,1)}, "
+                        "seed 2021",
+            "n_per_fill": n, "fills_per_step": len(ENGINES) * len(W.SWEEP_DISTS),
+            "parallelism": f"shard{world} (rank r fills words from r * words_for(n))",
+            "l2": "every fill writes 4-8 GB, larger than the 129 MB L2"}
+
+
 def run_reference(args):
     """The oracle as the reference arm: bounded samples of the sweep per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -452,11 +463,10 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32/f32/f64", "data": "synthetic",
-            "config": {"workload": "fill sweep (bounded CPU sample): Philox4x32-10 and "
-                                   "MRG32k3a x {bits u32, uniform f32/f64, gaussian f32/f64, "
-                                   "lognormal f32}, seed 2021", "samples_per_case": chunk * cores},
+            "config": sweep_config(int(args.n), args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample_desc},
+                             "sample": sample_desc + "; the rate stands for the sweep's "
+                                                     "samples/s"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -707,14 +717,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32/f64",
             "data": "synthetic",
-            "config": {"workload": f"fill sweep n={n:.0e} per GPU: Philox4x32-10 and MRG32k3a x "
-                                   "{bits u32, uniform f32 [0,1), uniform f64 [0,1), gaussian "
-                                   "f32 (0,1), gaussian f64 (0,1), lognormal f32 (0,1)}, "
-                                   "seed 2021",
-                       "n_per_fill": n, "fills_per_step": len(cases),
-                       "parallelism": f"shard{world} (rank r fills words from r * "
-                                      "words_for(n))",
-                       "l2": "every fill writes 4-8 GB, larger than the 129 MB L2"},
+            "config": sweep_config(n, world),
             "roofline": roofline,
             "target_philox_uniform_f32": {"write_gbs": target["write_gbs"],
                                           "frac": target["frac_hbm"],
