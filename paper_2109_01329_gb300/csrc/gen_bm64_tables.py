@@ -3,20 +3,18 @@
 Run from this directory: ``python gen_bm64_tables.py > bm64_tables.h``.
 Values are computed with mpmath at 200 bits and rounded to nearest.
 
-Tables (emitted as initializer macros GRNG_BM64_LOGC, _LOGT, _SINT, _COST)
-  kLogC[i], i = 0..512:  c_i = floor(2^24 / (1 - i/1024)) / 2^24, the reduction
-                         factor for -ln(1 - delta) with delta in [i/1024, (i+1)/1024)
-  kLogT[i]:              ln(c_i) * 2^64 (c_i exactly as stored)
-  kSinT[j], kCosT[j], j = 0..1024:  sin, cos(2 pi j / 8192) * 2^63
+Tables (emitted as initializer macros)
+  LT[i], i = 0..512:     (ln(c_i) * 2^64, c_i * 2^24) with c_i = floor(2^24 / (1 - i/1024))
+                         / 2^24, the reduction factor for -ln(1 - delta) with delta in
+                         [i/1024, (i+1)/1024)
+  SC[j], j = 0..1024:    (sin, cos(2 pi j / 8192)) * 2^63
   kE58[e], e = 0..52:    e ln 2 * 2^58
   kExp2T[j], j = 0..256: 2^(j / 256) * 2^62
 Scalars
   kLn2:    ln 2 * 2^64
   k2Pi61:  2 pi * 2^61
-  kLog2e63: log2(e) * 2^63,  kLn2_64 is kLn2
-  kInv2 .. kInv7: 2^64 / k (truncated)
-  kInv4_32 .. kInv7_32: 2^32 / k (truncated)
-  kInv24_32, kInv120_32, kInv720_32: 2^64 / 6 and 2^32 / {24, 120, 720}
+  kLog2e63: log2(e) * 2^63
+  kInv2 .. kInv6: 2^64 / k (truncated)
 """
 
 import mpmath as mp
@@ -55,23 +53,18 @@ def main():
     out.append(f"constexpr uint64_t kLn2 = {rnd(mp.log(2) * two64)}ull;")
     out.append(f"constexpr uint64_t k2Pi61 = {rnd(2 * mp.pi * mp.mpf(2) ** 61)}ull;")
     out.append(f"constexpr uint64_t kLog2e63 = {rnd(mp.log(mp.e, 2) * mp.mpf(2) ** 63)}ull;")
-    for k in range(2, 8):
+    for k in range(2, 7):
         out.append(f"constexpr uint64_t kInv{k} = {(1 << 64) // k}ull;")
-    out.append(f"constexpr uint32_t kInv24_32 = {rnd(mp.mpf(2) ** 32 / 24)}u;")
-    for k in (4, 5, 6, 7):
-        out.append(f"constexpr uint32_t kInv{k}_32 = {(1 << 32) // k}u;")
-    out.append(f"constexpr uint32_t kInv120_32 = {rnd(mp.mpf(2) ** 32 / 120)}u;")
-    out.append(f"constexpr uint32_t kInv720_32 = {rnd(mp.mpf(2) ** 32 / 720)}u;")
     # interleaved pairs, one 16-byte load each: (sin, cos) and (ln c_i, c_i)
     for name, a, b in (("SC", sint, cost), ("LT", logt, logc)):
         out.append(f"#define GRNG_BM64_{name} {{ \\")
         for k in range(0, len(a), 2):
             out.append("    " + ", ".join(f"{{{a[i]}ull, {b[i]}ull}}" for i in range(k, min(k + 2, len(a)))) + ", \\")
         out.append("}")
+    out.append(f"#define GRNG_BM64_LOGT_LEN {len(logt)}")
+    out.append(f"#define GRNG_BM64_SINT_LEN {len(sint)}")
     # table bodies as macros: the device and host copies are declared where used
-    for name, ctype, vals in [("LOGC", "uint32_t", logc), ("LOGT", "uint64_t", logt),
-                              ("SINT", "uint64_t", sint), ("COST", "uint64_t", cost),
-                              ("E58", "uint64_t", e58), ("EXP2T", "uint64_t", exp2t)]:
+    for name, ctype, vals in [("E58", "uint64_t", e58), ("EXP2T", "uint64_t", exp2t)]:
         suffix = "ull" if "64" in ctype else "u"
         out.append(f"#define GRNG_BM64_{name}_LEN {len(vals)}")
         out.append(f"#define GRNG_BM64_{name} {{ \\")
