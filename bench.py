@@ -743,7 +743,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=float, default=1e9)
-    ap.add_argument("--e2e-steps", type=int, default=3,
+    ap.add_argument("--e2e-steps", type=int, default=5,
                     help="timed end-to-end passes; the median one is reported")
     ap.add_argument("--cpu-seconds", type=float, default=1.5)
     ap.add_argument("--ref-samples", type=int, default=1 << 21)

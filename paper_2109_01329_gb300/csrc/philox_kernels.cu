@@ -19,6 +19,8 @@
 // geometry (each output is a function of its word index only).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cstdint>
 
 #include "device_common.cuh"
@@ -329,9 +331,14 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     } else {
       kernel = hi_uniform ? philox_stream_kernel<V, kU, true> : philox_stream_kernel<V, kU, false>;
     }
-    static int occ[2] = {0, 0};
-    int& o = occ[hi_uniform ? 1 : 0];
-    if (o == 0) o = blocks_per_sm(kernel);
+    // resident CTAs per SM, found once per kernel (atomic: launches may come
+    // from several host threads)
+    static std::atomic<int> occ[2] = {{0}, {0}};
+    int o = occ[hi_uniform ? 1 : 0].load(std::memory_order_relaxed);
+    if (o == 0) {
+      o = blocks_per_sm(kernel);
+      occ[hi_uniform ? 1 : 0].store(o, std::memory_order_relaxed);
+    }
     const int64_t work = (jl - jf + (int64_t)kU - 1) / kU;
     int64_t grid = (work + kThreads - 1) / kThreads;
     if (grid < 1) grid = 1;
@@ -350,8 +357,12 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.sb_hi = r.stride_hi >> 2;
     p.k0 = r.key[0];
     p.k1 = r.key[1];
-    static int occ = 0;
-    if (occ == 0) occ = blocks_per_sm(philox_multi_kernel<V>);
+    static std::atomic<int> occ_cache{0};
+    int occ = occ_cache.load(std::memory_order_relaxed);
+    if (occ == 0) {
+      occ = blocks_per_sm(philox_multi_kernel<V>);
+      occ_cache.store(occ, std::memory_order_relaxed);
+    }
     int64_t grid = (p.total + kThreads - 1) / kThreads;
     const int64_t cap = (int64_t)sms * occ;
     if (grid > cap) grid = cap;
@@ -379,8 +390,12 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.stride_hi = r.stride_hi;
     p.k0 = r.key[0];
     p.k1 = r.key[1];
-    static int occ = 0;
-    if (occ == 0) occ = blocks_per_sm(philox_staged_kernel<V>);
+    static std::atomic<int> occ_cache{0};
+    int occ = occ_cache.load(std::memory_order_relaxed);
+    if (occ == 0) {
+      occ = blocks_per_sm(philox_staged_kernel<V>);
+      occ_cache.store(occ, std::memory_order_relaxed);
+    }
     int64_t grid = p.num_streams * p.tiles_per_stream;
     const int64_t cap = (int64_t)sms * occ;
     if (grid > cap) grid = cap;
