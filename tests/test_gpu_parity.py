@@ -31,6 +31,7 @@ VARIANTS = [
     ("gauss_f32", 2, 1, 0.5, 2.0),
     ("logn_f32", 3, 1, 0.0, 1.0),
     ("gauss_f64", 2, 2, -1.0, 0.5),
+    ("gauss_f64_std", 2, 2, 0.0, 1.0),
     ("logn_f64", 3, 2, 0.25, 0.75),
     ("icdf_gauss_f32", 4, 1, 0.5, 2.0),
     ("icdf_logn_f32", 5, 1, 0.0, 1.0),
