@@ -315,7 +315,7 @@ def run_batched(grng, torch, dev, reps):
             e1.record(stream)
             e1.synchronize()
             loop_ms.append(e0.elapsed_time(e1))
-        b = grng.Batch(reqs, ipt=4, stream=stream)
+        b = grng.Batch(reqs, ipt=8, stream=stream)
         ctas, tune_ms = b.autotune(stream=stream)
         b.launch(stream=stream)
         stream.synchronize()
@@ -345,7 +345,7 @@ def run_batched(grng, torch, dev, reps):
             "batched_gsamples_s": round(total / med_batch / 1e6, 2),
             "batched_write_gbs": round(out_bytes / med_batch / 1e6, 1),
             "per_request_gsamples_s": round(total / med_loop / 1e6, 2),
-            "autotune": {"ctas_per_sm": ctas, "ms": round(tune_ms, 4), "ipt": 4},
+            "autotune": {"ctas_per_sm": ctas, "ms": round(tune_ms, 4), "ipt": 8},
             "reps": reps}
 
 

@@ -443,7 +443,7 @@ class Batch:
     device-resident offsets.
     """
 
-    def __init__(self, requests, ipt: int = 4, stream=None):
+    def __init__(self, requests, ipt: int = 8, stream=None):
         import torch
 
         self._reqs = list(requests)
