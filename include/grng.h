@@ -100,8 +100,9 @@ typedef enum grng_dtype { GRNG_U32 = 0, GRNG_F32 = 1, GRNG_F64 = 2 } grng_dtype;
  *             only for quasi-random generators, Sec. 3.1): one uniform per
  *             output, u = (k + 1/2) 2^-23 with k = w >> 9 (F32) or
  *             u = (x + 1/2) 2^-52 with x = ((w_a << 32 | w_b) >> 12) (F64),
- *             z = Phi^-1(u) (CUDA's normcdfinvf for F32; a fixed-point
- *             piecewise polynomial in sqrt(-2 ln min(u, 1 - u)) for F64).
+ *             z = Phi^-1(u) (F32: x P(-log2(1 - x^2)) with x = 2u - 1, two
+ *             polynomial branches as in Giles's erfinv; F64: a fixed-point
+ *             piecewise polynomial in sqrt(-2 ln min(u, 1 - u))).
  * Uniform and bits outputs are bit-exact functions of the words; gaussian and
  * lognormal outputs are within 2e-6 max(1, |x|) (F32) or 1e-14 max(1, |x|)
  * (F64) of the exact value (F64 lognormal: for |s z| up to about 10; beyond

@@ -7,6 +7,7 @@
 
 #include "bm64_fixed.cuh"
 #include "grng_internal.h"
+#include "icdf32_tables.h"
 #include "icdf64_fixed.cuh"
 
 namespace grng {
@@ -119,13 +120,13 @@ __device__ __forceinline__ double range_f64(double u, const TransformParams& t) 
 // coefficients come from gen_bm32_poly.py (fits on Chebyshev nodes refined
 // towards minimax, rounded to float).
 //
-// -2 ln u1 for u1 = j 2^-24, j = (w >> 8) + 1 in [1, 2^24]: j = 2^e m with m
+// -2 ln(j 2^-24) for j in [1, 2^24] (the Box-Muller u1 has j = (w >> 8) + 1): j = 2^e m with m
 // in [sqrt(1/2), sqrt(2)) split from the float's bits, t = m - 1 (exact),
 // ln m = t + t^2 P(t) (P of degree 7, relative error below 3e-8), and
 // -2 ln u1 = 2 ((24 - e) ln 2 - ln m): no cancellation as u1 -> 1 (e = 24).
 // Over all 2^24 inputs the relative error stays below 1e-7.
-__device__ __forceinline__ float neg2_log_u1_f32(uint32_t w) {
-  const float f = __uint2float_rn((w >> 8) + 1u);  // exact
+__device__ __forceinline__ float neg2_log_j_f32(uint32_t j) {
+  const float f = __uint2float_rn(j);  // exact
   const int ix = __float_as_int(f);
   const int e = (ix - 0x3F3504F3) >> 23;
   const float t = __int_as_float(ix - (e << 23)) - 1.0f;
@@ -142,6 +143,7 @@ __device__ __forceinline__ float neg2_log_u1_f32(uint32_t w) {
   const float k = __int_as_float(0x4B000000 + 24 - e) - 8388608.0f;
   return 2.0f * fmaf(k, 0.693147182464599609375f, -lnm);
 }
+__device__ __forceinline__ float neg2_log_u1_f32(uint32_t w) { return neg2_log_j_f32((w >> 8) + 1u); }
 
 // sin and cos of 2 pi k 2^-24, k = w >> 8: octant o = k >> 21, the position
 // t in [0, 2^21] within it (reflected in odd octants), v = t 2^-21 (exact),
@@ -171,6 +173,48 @@ __device__ __forceinline__ void sincos_turns_f32(uint32_t w, float& s, float& c)
   c = (((o + 2u) & 4u) != 0) ? -b : b;  // octants 2, 3, 4, 5
 }
 
+// FP32 inverse CDF of the standard normal for u = (k + 1/2) 2^-23, k = w >> 9
+// (polynomials in icdf32_tables.h, written by gen_icdf32_tables.py).  With
+// x = 2u - 1 = (2k + 1 - 2^23) 2^-23 (exact) and v = -log2(1 - x^2),
+// Phi^-1(u) = sqrt(2) erfinv(x) = x P(v): P1(v) of degree 9 below
+// v = 5 / ln 2 (|x| < 0.9966, 99.7% of outputs, so warps rarely diverge) and
+// P2(sqrt(v) - sqrt(5 / ln 2)) of degree 8 above (Giles's form of erfinv).
+// 1 - x^2 comes from one FMA of the exact x (one rounding) and v from the
+// hardware lg2.approx: z depends on v only through x P'(v), so the absolute
+// error of lg2.approx (about 2^-22) moves z by a few 1e-8.  Emulated over all
+// 2^23 inputs with twice that log error the result stays within 2.2e-7 of
+// max(1, |z|) from the exact value.
+// The central polynomial for every input, so that a thread's several inverse
+// CDFs run as straight-line code; the rare tail input redoes r afterwards.
+struct Icdf32 {
+  float x, v, r;
+};
+__device__ __forceinline__ Icdf32 icdf_f32_central(uint32_t w) {
+  Icdf32 c;
+  // 2^23 + k by the 2^23 shifter, then x = (k 2^-22 - 1) + 2^-23: both steps exact
+  const float f = __int_as_float(0x4B000000u | (w >> 9));
+  c.x = fmaf(f, 0x1p-22f, -3.0f) + 0x1p-23f;
+  const float q = fmaf(-c.x, c.x, 1.0f);  // 1 - x^2 in [2^-22, 1]
+  float lg;
+  asm("lg2.approx.f32 %0, %1;" : "=f"(lg) : "f"(q));
+  c.v = -lg;
+  c.r = GRNG_ICDF32_P1(c.v);
+  return c;
+}
+__device__ __forceinline__ bool icdf_f32_is_tail(const Icdf32& c) { return c.v >= GRNG_ICDF32_V1; }
+__device__ __forceinline__ void icdf_f32_tail(Icdf32& c) {
+  float sv;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(sv) : "f"(c.v));
+  const float d = sv - GRNG_ICDF32_SQRT_V1;
+  c.r = GRNG_ICDF32_P2(d);
+}
+__device__ __forceinline__ float icdf_f32_finish(const Icdf32& c) { return c.x * c.r; }
+__device__ __forceinline__ float icdf_f32(uint32_t w) {
+  Icdf32 c = icdf_f32_central(w);
+  if (icdf_f32_is_tail(c)) icdf_f32_tail(c);
+  return icdf_f32_finish(c);
+}
+
 // rho = sqrt(-2 ln u1) by the hardware square root (relative error about
 // 2^-23; its argument is 0 or at least -2 ln(1 - 2^-24) > 1e-7, never
 // subnormal), z0 = rho cos(2 pi u2), z1 = rho sin(2 pi u2).
@@ -189,6 +233,14 @@ __device__ __forceinline__ void box_muller_f32(uint32_t w0, uint32_t w1, float& 
 __device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
                                                double& z0, double& z1) {
   bm64::box_muller(u53(w0, w1), u53(w2, w3), z0, z1);
+}
+
+// mean + sd z, or exp of it, as the output word of an inverse-CDF variant
+template <int V>
+__device__ __forceinline__ uint32_t icdf_out_f32(float z, const TransformParams& t) {
+  float y = fmaf(t.fsd, z, t.fmean);
+  if constexpr (V == V_ICDF_LOGN_F32) y = expf(y);
+  return __float_as_uint(y);
 }
 
 // ------------------------------------------------- one unit -> its outputs
@@ -227,10 +279,7 @@ __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
     o[1] = __float_as_uint(y1);
   } else if constexpr (V == V_ICDF_GAUSS_F32 || V == V_ICDF_LOGN_F32) {
     // u = (k + 1/2) 2^-23, k = w >> 9: an exact midpoint in (0, 1)
-    const float u = __uint2float_rn(2u * (w[0] >> 9) + 1u) * 0x1p-24f;
-    float y = fmaf(t.fsd, normcdfinvf(u), t.fmean);
-    if constexpr (V == V_ICDF_LOGN_F32) y = expf(y);
-    o[0] = __float_as_uint(y);
+    o[0] = icdf_out_f32<V>(icdf_f32(w[0]), t);
   } else if constexpr (V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64) {
     // u = (x + 1/2) 2^-52, x = ((w_a << 32) | w_b) >> 12; Phi^-1 in fixed
     // point (icdf64_fixed.cuh), then mean + sd z or exp(m + s z) as for the
@@ -297,8 +346,23 @@ __device__ __forceinline__ uint4 block_outputs(uint4 b, const TransformParams& t
                                                                  : 2;
   uint32_t w[4] = {b.x, b.y, b.z, b.w};
   uint32_t o[4];
+  if constexpr (V == V_ICDF_GAUSS_F32 || V == V_ICDF_LOGN_F32) {
+    // the four central evaluations interleave; one vote skips the tails
+    Icdf32 c[4];
 #pragma unroll
-  for (int u = 0; u < 4 / kWpu; ++u) unit_outputs<V>(w + u * kWpu, o + u * kWpu, t);
+    for (int u = 0; u < 4; ++u) c[u] = icdf_f32_central(w[u]);
+    if (icdf_f32_is_tail(c[0]) | icdf_f32_is_tail(c[1]) | icdf_f32_is_tail(c[2]) |
+        icdf_f32_is_tail(c[3])) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (icdf_f32_is_tail(c[u])) icdf_f32_tail(c[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) o[u] = icdf_out_f32<V>(icdf_f32_finish(c[u]), t);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4 / kWpu; ++u) unit_outputs<V>(w + u * kWpu, o + u * kWpu, t);
+  }
   return make_uint4(o[0], o[1], o[2], o[3]);
 }
 

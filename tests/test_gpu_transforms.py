@@ -188,10 +188,16 @@ def test_transform_odd_n_and_random(g, var):
 
 @pytest.mark.parametrize("kind,p0,p1", [(4, 0.0, 1.0), (5, 0.0, 1.0), (4, -1.0, 3.0)])
 def test_icdf_f32_tails_and_sweep(g, kind, p0, p1):
-    """Every k in both tails (k < 4096 and k > 2^23 - 4096) and every 61st k
-    in between: the inverse CDF meets the FP32 tolerance across (0, 1)."""
+    """Every k in both tails (k < 4096 and k > 2^23 - 4096), every k within
+    2048 of the centre and of the two points where the kernel switches from
+    its central to its tail polynomial (-log2(1 - x^2) = 5 / ln 2 with
+    x = 2u - 1), and every 61st k in between: the inverse CDF meets the FP32
+    tolerance across (0, 1)."""
+    x1 = np.sqrt(1.0 - np.exp(-5.0))
+    seams = [int(((1 << 23) * (1.0 + s * x1) - 1.0) / 2.0) for s in (-1.0, 1.0)] + [1 << 22]
     k = np.concatenate([np.arange(0, 4096), np.arange((1 << 23) - 4096, 1 << 23),
-                        np.arange(4096, (1 << 23) - 4096, 61)]).astype(np.uint32)
+                        np.arange(4096, (1 << 23) - 4096, 61)]
+                       + [np.arange(c - 2048, c + 2048) for c in seams]).astype(np.uint32)
     w = (k << np.uint32(9)) | np.uint32(0x155)
     got = _gpu(g, kind, 1, p0, p1, w, w.size)
     ref = oracle.transform_words(kind, 1, p0, p1, w.size, w)
