@@ -287,7 +287,7 @@ def run_extra(grng, torch, dev, n, buf, stream, reps, hbm_peak):
 
 
 def run_batched(grng, torch, dev, reps):
-    """Config 4: 4096 Philox engines (seeds 1..4096), log-uniform sizes in
+    """Batched requests: 4096 Philox engines (seeds 1..4096), log-uniform sizes in
     [64, 2^20], five distributions; one graph-replayed persistent launch vs
     one grng_generate launch per request (back to back on one stream)."""
     table = W.batched_requests(4096)
@@ -350,7 +350,7 @@ def run_batched(grng, torch, dev, reps):
 
 
 def run_serving(grng, torch, dev, seconds, stress):
-    """Config 5: FastCaloSim-shaped serving.  Poisson arrivals at 2000 events/s,
+    """FastCaloSim-shaped serving.  Poisson arrivals at 2000 events/s,
     hits ~ lognormal(mean 8000, sigma 0.8) clipped to [100, 200000]; each event
     = 3h FP32 uniforms + h FP32 gaussians from its own Philox engine (seed =
     event id); 4 GB admission budget; replayed in real time, then compressed

@@ -36,8 +36,9 @@ SWEEP_DISTS = [
 SWEEP_SIZES = [10**6, 10**7, 10**8, 10**9]
 SWEEP_SEED = 2021
 
-CONFIG1 = dict(engine=0, seed=0x12345678, offset=0, n=1 << 20, dist=("uniform_f32", UNIFORM, F32,
-                                                                      0.0, 1.0))
+# Philox seed 0x12345678, offset 0, 2^20 FP32 uniforms on [0, 1): compared bit for bit
+PHILOX_UNIFORM_2POW20 = dict(engine=0, seed=0x12345678, offset=0, n=1 << 20,
+                             dist=("uniform_f32", UNIFORM, F32, 0.0, 1.0))
 
 SUBSTREAMS = dict(num_streams=16384, n_per_stream=65536, seed=2021, mrg_stride=1 << 76,
                   philox_stride=1 << 40, dist=("gaussian_f64", GAUSSIAN, F64, 0.0, 1.0))

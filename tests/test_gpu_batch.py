@@ -4,8 +4,8 @@ A batch must give every request exactly what the same grng_generate calls in
 table order would give (requests of one engine follow each other in its
 sequence), continue every sequence on the next launch (device-resident
 offsets), replay identically from a CUDA graph, and leave the engines at the
-right offsets after commit.  Config 4: 4096 Philox engines, log-uniform sizes
-in [64, 2^20], five distributions.
+right offsets after commit.  The full table: 4096 Philox engines, log-uniform
+sizes in [64, 2^20], five distributions.
 """
 
 import numpy as np
@@ -162,7 +162,7 @@ def test_autotune_keeps_outputs(g):
         assert torch.equal(x.view(torch.uint8), r[2].view(torch.uint8))
 
 
-def test_config4_batch_equals_per_request(g):
+def test_4096_request_batch_equals_per_request(g):
     table = W.batched_requests(4096)
     outs, reqs, singles = [], [], []
     for q in table:

@@ -122,12 +122,12 @@ def test_small_cases_all_variants(g, engine_kind, var):
         assert_parity(var[1], var[2], got, ref, f"{var[0]} n={n} off={off} ptr+{pofs}")
 
 
-def test_config1_bit_exact(g):
-    c = W.CONFIG1
+def test_philox_uniform_2pow20_bit_exact(g):
+    c = W.PHILOX_UNIFORM_2POW20
     var = c["dist"]
     got = _gpu_fill(g, c["engine"], c["seed"], c["offset"], var, c["n"])
     ref = _ref(c["engine"], c["seed"], c["offset"], var, c["n"])
-    assert_parity(var[1], var[2], got, ref, "config 1")
+    assert_parity(var[1], var[2], got, ref, "Philox 2^20 FP32 uniform")
 
 
 @pytest.mark.parametrize("engine_kind", ENGINES)
@@ -172,7 +172,7 @@ def test_sweep_1e9_windows(g, engine_kind, var):
 
 
 @pytest.mark.parametrize("engine_kind,stride", [(1, 1 << 76), (0, 1 << 40)])
-def test_config3_substreams(g, engine_kind, stride):
+def test_16384_substreams(g, engine_kind, stride):
     c = W.SUBSTREAMS
     S, n = c["num_streams"], c["n_per_stream"]
     _, kind, dtype, p0, p1 = c["dist"]

@@ -47,7 +47,7 @@ def test_empty_and_invalid():
         oracle.generate(5, 1, 0, DIST_UNIFORM, DT_F32, 0.0, 1.0, 4)
 
 
-def test_config1_head_is_stable():
+def test_philox_uniform_2pow20_head_is_stable():
     """Philox seed 0x12345678, offset 0, 2^20 FP32 uniforms: the first values
     equal the Triton-pinned Philox words through the exact conversion."""
     u = oracle.generate(oracle.ENGINE_PHILOX, 0x12345678, 0, DIST_UNIFORM, DT_F32, 0.0, 1.0,
