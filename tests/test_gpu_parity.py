@@ -288,3 +288,24 @@ def test_seed_word_engines(g, engine_kind):
             got = out.cpu().numpy()
             assert_parity(kind, dtype, got.view(np.uint32) if dtype == 0 else got, ref,
                           f"words {words} {var[0]}")
+
+
+@pytest.mark.parametrize("engine_kind", ENGINES)
+@pytest.mark.parametrize("var", VARIANTS, ids=[v[0] for v in VARIANTS])
+@pytest.mark.parametrize("n,offset,ptr_off", [(3 * (1 << 20) + 5, 0, 0), (1 << 20, 3, 1)])
+def test_fill_equals_transform_of_its_words(g, engine_kind, var, n, offset, ptr_off):
+    """The fused fill kernels (one counter block per 16-byte group, the staged
+    phase, MRG32k3a's chunked copy-out, the inverse CDF's four-at-a-time
+    block form) and the transform kernel are separate code; applied to the
+    same engine words they must agree bit for bit."""
+    _, kind, dtype, p0, p1 = var
+    got = _gpu_fill(g, engine_kind, 2021, offset, var, n, ptr_off=ptr_off)
+    nw = oracle.words_for(kind, dtype, n)
+    words = _gpu_fill(g, engine_kind, 2021, offset, ("bits", 0, 0, 0.0, 0.0), nw)
+    w = torch.from_numpy(words.view(np.int32)).cuda()
+    out = torch.empty(n, dtype=_torch_dtype(dtype), device="cuda")
+    g.transform_words(g.Distribution(kind, dtype, p0, p1), w, out)
+    torch.cuda.synchronize()
+    ref = out.cpu().numpy()
+    bad = np.nonzero(_as_uint_view(got) != _as_uint_view(ref))[0]
+    assert bad.size == 0, f"{var[0]}: {bad.size} differ, first at {bad[:5]}"

@@ -205,6 +205,25 @@ def test_icdf_f32_tails_and_sweep(g, kind, p0, p1):
     print(f"ICDF FP32 kind {kind}: worst error / max(1,|x|) = {worst:.3e}")
 
 
+@pytest.mark.parametrize("kind,p0,p1", [(4, 0.0, 1.0), (5, 0.0, 1.0)])
+def test_icdf_f32_all_2_23(g, kind, p0, p1):
+    """All 2^23 FP32 inverse-CDF inputs u = (k + 1/2) 2^-23 (the 9 low word
+    bits, which the method drops, vary with k) against the oracle, computed
+    in chunks on the host's cores."""
+    import concurrent.futures as cf
+    import os
+
+    k = np.arange(1 << 23, dtype=np.uint32)
+    w = (k << np.uint32(9)) | ((k * np.uint32(0x9E3779B1)) >> np.uint32(23))
+    got = _gpu(g, kind, 1, p0, p1, w, w.size)
+    chunks = np.array_split(w, 64)
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        parts = list(ex.map(lambda c: oracle.transform_words(kind, 1, p0, p1, c.size, c), chunks))
+    ref = np.concatenate(parts)
+    worst = _check(kind, 1, got, ref, f"ICDF FP32 kind {kind}, all inputs")
+    print(f"ICDF FP32 kind {kind}, all 2^23 inputs: worst error / max(1,|x|) = {worst:.3e}")
+
+
 @pytest.mark.parametrize("kind", [4, 5])
 def test_icdf_f64_tails(g, kind):
     rng = np.random.Generator(np.random.PCG64(8))
