@@ -189,7 +189,9 @@ GRNG_BM_HD float fma32(float a, float b, float c) {
 
 GRNG_BM_HD float rsqrt_seed(float x) {
 #if defined(__CUDA_ARCH__)
-  return rsqrtf(x);
+  float y;  // x in [1/4, 1): never subnormal, so the flush-to-zero form
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 #else
   return 1.0f / std::sqrt(x);
 #endif

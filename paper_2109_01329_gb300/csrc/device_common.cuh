@@ -180,12 +180,13 @@ __device__ __forceinline__ void sincos_turns_f32(uint32_t w, float& s, float& c)
 // v = 5 / ln 2 (|x| < 0.9966, 99.7% of outputs, so warps rarely diverge) and
 // P2(sqrt(v) - sqrt(5 / ln 2)) of degree 8 above (Giles's form of erfinv).
 // 1 - x^2 comes from one FMA of the exact x (one rounding) and v from the
-// hardware lg2.approx: z depends on v only through x P'(v), so the absolute
-// error of lg2.approx (about 2^-22) moves z by a few 1e-8.  Emulated over all
-// 2^23 inputs with twice that log error the result stays within 2.2e-7 of
-// max(1, |z|) from the exact value.
-// The central polynomial for every input, so that a thread's several inverse
-// CDFs run as straight-line code; the rare tail input redoes r afterwards.
+// hardware lg2.approx (flush-to-zero form: q is never subnormal).  z depends
+// on v only through x P'(v), so the absolute error of lg2.approx (about
+// 2^-22) moves z by a few 1e-8: emulated over all 2^23 inputs with twice that
+// log error the result stays within 2.2e-7 of max(1, |z|) from the exact
+// value.  The central polynomial runs for every input, so that a thread's
+// several inverse CDFs are straight-line code; the rare tail input redoes r
+// afterwards.
 struct Icdf32 {
   float x, v, r;
 };
@@ -196,7 +197,7 @@ __device__ __forceinline__ Icdf32 icdf_f32_central(uint32_t w) {
   c.x = fmaf(f, 0x1p-22f, -3.0f) + 0x1p-23f;
   const float q = fmaf(-c.x, c.x, 1.0f);  // 1 - x^2 in [2^-22, 1]
   float lg;
-  asm("lg2.approx.f32 %0, %1;" : "=f"(lg) : "f"(q));
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(q));
   c.v = -lg;
   c.r = GRNG_ICDF32_P1(c.v);
   return c;
@@ -204,7 +205,7 @@ __device__ __forceinline__ Icdf32 icdf_f32_central(uint32_t w) {
 __device__ __forceinline__ bool icdf_f32_is_tail(const Icdf32& c) { return c.v >= GRNG_ICDF32_V1; }
 __device__ __forceinline__ void icdf_f32_tail(Icdf32& c) {
   float sv;
-  asm("sqrt.approx.f32 %0, %1;" : "=f"(sv) : "f"(c.v));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sv) : "f"(c.v));
   const float d = sv - GRNG_ICDF32_SQRT_V1;
   c.r = GRNG_ICDF32_P2(d);
 }
@@ -217,11 +218,12 @@ __device__ __forceinline__ float icdf_f32(uint32_t w) {
 
 // rho = sqrt(-2 ln u1) by the hardware square root (relative error about
 // 2^-23; its argument is 0 or at least -2 ln(1 - 2^-24) > 1e-7, never
-// subnormal), z0 = rho cos(2 pi u2), z1 = rho sin(2 pi u2).
+// subnormal, so the flush-to-zero form, which skips the subnormal handling),
+// z0 = rho cos(2 pi u2), z1 = rho sin(2 pi u2).
 __device__ __forceinline__ void box_muller_f32(uint32_t w0, uint32_t w1, float& z0, float& z1) {
   const float v = neg2_log_u1_f32(w0);
   float rho;
-  asm("sqrt.approx.f32 %0, %1;" : "=f"(rho) : "f"(v));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rho) : "f"(v));
   float s, c;
   sincos_turns_f32(w1, s, c);
   z0 = rho * c;
