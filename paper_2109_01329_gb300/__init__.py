@@ -1,8 +1,10 @@
 """grng: bulk random number generation on GB300 (sm_103a).
 
-Engines (Philox4x32-10, MRG32k3a) and distributions (bits, uniform, Box-Muller
-gaussian, lognormal) behind the C ABI of include/grng.h, implemented by
-hand-written CUDA kernels in csrc/.  This package is the thin Python binding.
+Engines (Philox4x32-10, MRG32k3a) and distributions (bits, uniform, gaussian
+and lognormal by Box-Muller or by the inverse CDF) behind the C ABI of
+include/grng.h, implemented by hand-written CUDA kernels in csrc/, with the
+batched (Batch) and served (Server) forms.  This package is the thin Python
+binding.
 """
 
 from ._binding import (BITS, GAUSSIAN_ICDF, LOGNORMAL_ICDF, Batch, Server, serve_request, F32, F64, GAUSSIAN, LOGNORMAL, MRG32K3A, PHILOX4X32X10, U32,
