@@ -107,11 +107,14 @@ __device__ __forceinline__ uint4 assemble_group(const uint32_t* swords, int64_t 
 
 // The groups [g0, g0 + kThreads ipt) of one request (the whole CTA works on
 // one tile, so every branch below is uniform across it).  Group 0 starts
-// head elements (pw = head es / 4 words) before the output; when off - pw is
-// a multiple of 4 and pw of the unit size, group g is exactly Philox block
-// (off - pw)/4 + g.  Otherwise each slice of kThreads groups stages the
-// blocks its words span in shared memory (about one block per thread) and
-// each thread assembles its group from there.
+// head elements (pw = head es / 4 words) before the output.  When pw is a
+// multiple of the unit size, group g is the 4 words from word off - pw + 4 g:
+// exactly Philox block (off - pw)/4 + g when off - pw is a multiple of 4,
+// else the tail of one block and the head of the next, exchanged between
+// neighbouring lanes.  Otherwise (a Box-Muller pair split by the output's
+// start) each slice of kThreads groups stages the blocks its words span in
+// shared memory (about one block per thread) and each thread assembles its
+// group from there.
 template <int V>
 __device__ __forceinline__ void batch_tile(const BatchReq& r, uint64_t off_lo, uint64_t off_hi,
                                            int64_t g0, int ipt, uint4* sblocks) {
@@ -123,16 +126,49 @@ __device__ __forceinline__ void batch_tile(const BatchReq& r, uint64_t off_lo, u
   char* base = reinterpret_cast<char*>(r.out);
   const TransformParams t = r.t;
   const uint32_t pw = (uint32_t)head * (uint32_t)(I::es / 4);
-  if (((off_lo - pw) & 3u) == 0 && (pw % (uint32_t)kWpu) == 0) {
+  if ((pw % (uint32_t)kWpu) == 0) {
+    // group g is the 4 words from word off - pw + 4 g: the block of that
+    // word from phase ph on, and the first ph words of the next block
     const uint64_t a_lo = off_lo - pw, a_hi = off_hi - ((off_lo < pw) ? 1u : 0u);
     const uint64_t b_lo = (a_lo >> 2) | (a_hi << 62), b_hi = a_hi >> 2;
-    for (int i = 0; i < ipt; ++i) {
-      const int64_t g = g0 + (int64_t)i * kThreads + threadIdx.x;
-      if (g >= groups) break;
+    const uint32_t ph = (uint32_t)a_lo & 3u;
+    if (ph == 0) {
+      for (int i = 0; i < ipt; ++i) {
+        const int64_t g = g0 + (int64_t)i * kThreads + threadIdx.x;
+        if (g >= groups) break;
+        const uint64_t c_lo = b_lo + (uint64_t)g;
+        const uint64_t c_hi = b_hi + ((c_lo < b_lo) ? 1u : 0u);
+        const uint4 o = block_outputs<V>(philox4x32_10(ctr_from(c_lo, c_hi), k0, k1), t);
+        store_group<V>(base, g * kEpg - head, n, o);
+      }
+      return;
+    }
+    // Each warp computes 32 consecutive blocks and emits the 31 groups that
+    // start in its lanes 0..30, taking the next block's words from lane + 1
+    // by shuffle: no shared memory and no barrier.  The loop bound depends
+    // only on the warp, so every shuffle has all 32 lanes.
+    const int lane = threadIdx.x & 31;
+    const int64_t g_end = (g0 + (int64_t)kThreads * ipt) < groups ? (g0 + (int64_t)kThreads * ipt)
+                                                                   : groups;
+    constexpr int kPerWarp = 31;
+    for (int64_t gs = g0 + (int64_t)(threadIdx.x >> 5) * kPerWarp; gs < g_end;
+         gs += (int64_t)kPerWarp * (kThreads / 32)) {
+      const int64_t g = gs + lane;
       const uint64_t c_lo = b_lo + (uint64_t)g;
       const uint64_t c_hi = b_hi + ((c_lo < b_lo) ? 1u : 0u);
-      const uint4 o = block_outputs<V>(philox4x32_10(ctr_from(c_lo, c_hi), k0, k1), t);
-      store_group<V>(base, g * kEpg - head, n, o);
+      const uint4 b = philox4x32_10(ctr_from(c_lo, c_hi), k0, k1);
+      const uint32_t n0 = __shfl_down_sync(0xFFFFFFFFu, b.x, 1);
+      const uint32_t n1 = __shfl_down_sync(0xFFFFFFFFu, b.y, 1);
+      const uint32_t n2 = __shfl_down_sync(0xFFFFFFFFu, b.z, 1);
+      uint4 w;
+      if (ph == 1) {
+        w = make_uint4(b.y, b.z, b.w, n0);
+      } else if (ph == 2) {
+        w = make_uint4(b.z, b.w, n0, n1);
+      } else {
+        w = make_uint4(b.w, n0, n1, n2);
+      }
+      if (lane < kPerWarp && g < g_end) store_group<V>(base, g * kEpg - head, n, block_outputs<V>(w, t));
     }
     return;
   }

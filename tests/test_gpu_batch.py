@@ -162,17 +162,24 @@ def test_autotune_keeps_outputs(g):
         assert torch.equal(x.view(torch.uint8), r[2].view(torch.uint8))
 
 
-def test_4096_request_batch_equals_per_request(g):
+@pytest.mark.parametrize("phased", [False, True], ids=["offset0", "word_phases"])
+def test_4096_request_batch_equals_per_request(g, phased):
+    """The 4096-request table, bit for bit against one grng_generate per
+    request; with phased engines every request starts at a word offset of
+    random phase mod 4 (the state of engines that have run before), so the
+    groups straddle Philox blocks."""
     table = W.batched_requests(4096)
+    rng0 = np.random.Generator(np.random.PCG64(77))
+    offs = rng0.integers(0, 1 << 40, len(table)) if phased else np.zeros(len(table), np.int64)
     outs, reqs, singles = [], [], []
-    for q in table:
+    for q, off in zip(table, offs):
         name, kind, dtype, p0, p1 = q["dist"]
         n = q["n"]
         d = g.Distribution(kind, dtype, p0, p1)
         out = torch.empty(n, dtype=TDT[dtype], device="cuda")
-        reqs.append((g.Engine(0, q["seed"], 0), d, out, n))
+        reqs.append((g.Engine(0, q["seed"], int(off)), d, out, n))
         ref = torch.empty(n, dtype=TDT[dtype], device="cuda")
-        g.generate(d, g.Engine(0, q["seed"], 0), ref)
+        g.generate(d, g.Engine(0, q["seed"], int(off)), ref)
         singles.append(ref)
     b = g.Batch(reqs, ipt=4)
     b.autotune()
@@ -187,5 +194,5 @@ def test_4096_request_batch_equals_per_request(g):
         q = table[int(i)]
         name, kind, dtype, p0, p1 = q["dist"]
         m = min(q["n"], 4096)
-        ref = oracle.generate(0, q["seed"], 0, kind, dtype, p0, p1, m)
+        ref = oracle.generate(0, q["seed"], int(offs[int(i)]), kind, dtype, p0, p1, m)
         assert _close(kind, dtype, _host(reqs[int(i)][2][:m]), ref)
