@@ -12,7 +12,12 @@
 //     its block boundary (and Box-Muller pairs do not straddle groups), group
 //     j is exactly Philox block base + j: one block, one transform, one
 //     st.v4.  Only the first and the last group of a stream may be partial.
-//   * staged kernel: any other phase.  A CTA computes the blocks covering a
+//   * shift kernel (one stream whose output starts on a unit boundary, any
+//     other word phase): group j is the tail of block base + j and the head
+//     of block base + j + 1; a warp computes 32 consecutive blocks and emits
+//     31 groups, exchanging the words between neighbouring lanes by shuffle.
+//   * staged kernel: the rest (substreams at another phase, a Box-Muller pair
+//     split by the output's start).  A CTA computes the blocks covering a
 //     tile of 256 groups into shared memory, then each thread assembles its
 //     group from the words it needs.
 // Both write every output exactly once; results do not depend on the launch
@@ -126,6 +131,84 @@ __global__ void __launch_bounds__(kThreads) philox_stream_kernel(const StreamPar
 template <int V, int U, bool kHiUniform>
 __global__ void __launch_bounds__(kThreads, 5) philox_stream_kernel_5(const StreamParams p) {
   philox_stream_body<V, U, kHiUniform>(p);
+}
+
+// ------------------------------------------------------ single stream, shifted
+// The same groups when the word offset is not on a block boundary (phase
+// ph = 1..3 after removing the head words): group j is the last 4 - ph words
+// of block base + j and the first ph words of block base + j + 1.  Each warp
+// computes 32 consecutive blocks and emits the 31 groups that start in its
+// lanes 0..30, taking the next block's words from lane + 1 by shuffle, so a
+// group still costs 32/31 of a block and no shared memory or barrier.  U
+// chunks of 31 groups per warp per iteration, as U blocks per thread above.
+struct ShiftParams {
+  TransformParams t;
+  uint4* gbase;       // 16-byte aligned address of group 0 (may precede out)
+  void* out;
+  int64_t n;          // elements
+  int64_t head;       // elements of group 0 that lie before out
+  int64_t groups;
+  int64_t chunks;     // ceil(groups / 31)
+  uint64_t base_lo;   // block holding the first word of group 0
+  uint64_t base_hi;
+  uint32_t ph;        // 1..3
+  uint32_t k0, k1;
+};
+
+constexpr int kShiftPerWarp = 31;
+
+template <int V, int U, bool kHiUniform>
+__device__ __forceinline__ void philox_shift_body(const ShiftParams& p) {
+  using I = VInfo<V>;
+  constexpr int kEpg = 16 / I::es;
+  const int lane = threadIdx.x & 31;
+  const int64_t TW = (int64_t)gridDim.x * (kThreads / 32);
+  // the loop bound depends only on the warp: every shuffle has all 32 lanes
+  for (int64_t c = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); c < p.chunks;
+       c += U * TW) {
+    uint4 b[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t j = (uint64_t)((c + u * TW) * kShiftPerWarp + lane);
+      const uint64_t lo = p.base_lo + j;
+      const uint64_t hi = kHiUniform ? p.base_hi : p.base_hi + ((lo < p.base_lo) ? 1u : 0u);
+      b[u] = philox4x32_10(ctr_from(lo, hi), p.k0, p.k1);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t n0 = __shfl_down_sync(0xFFFFFFFFu, b[u].x, 1);
+      const uint32_t n1 = __shfl_down_sync(0xFFFFFFFFu, b[u].y, 1);
+      const uint32_t n2 = __shfl_down_sync(0xFFFFFFFFu, b[u].z, 1);
+      uint4 w;
+      if (p.ph == 1) {
+        w = make_uint4(b[u].y, b[u].z, b[u].w, n0);
+      } else if (p.ph == 2) {
+        w = make_uint4(b[u].z, b[u].w, n0, n1);
+      } else {
+        w = make_uint4(b[u].w, n0, n1, n2);
+      }
+      const int64_t j = (c + u * TW) * kShiftPerWarp + lane;
+      if (lane < kShiftPerWarp && j < p.groups) {
+        const uint4 o = block_outputs<V>(w, p.t);
+        const int64_t e0 = j * kEpg - p.head;
+        if (e0 >= 0 && e0 + kEpg <= p.n) {
+          p.gbase[j] = o;
+        } else {
+          store_partial<V>(reinterpret_cast<char*>(p.out), e0, p.n, o);
+        }
+      }
+    }
+  }
+}
+
+template <int V, int U, bool kHiUniform>
+__global__ void __launch_bounds__(kThreads) philox_shift_kernel(const ShiftParams p) {
+  philox_shift_body<V, U, kHiUniform>(p);
+}
+
+template <int V, int U, bool kHiUniform>
+__global__ void __launch_bounds__(kThreads, 5) philox_shift_kernel_5(const ShiftParams p) {
+  philox_shift_body<V, U, kHiUniform>(p);
 }
 
 // ------------------------------------------------------------ substreams
@@ -375,6 +458,56 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.tqsb_lo = (uint64_t)tqsb;
     p.tqsb_hi = (uint64_t)(tqsb >> 64);
     philox_multi_kernel<V><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+  } else if (r.num_streams == 1 && (phase_w % (uint32_t)I::wpu) == 0) {
+    // a word phase other than the pointer's, units not split by the start
+    ShiftParams p;
+    p.t = r.t;
+    p.out = r.out;
+    p.gbase = reinterpret_cast<uint4*>(addr - phase_w * 4u);
+    p.n = r.n;
+    p.head = head;
+    p.groups = groups;
+    p.chunks = (groups + kShiftPerWarp - 1) / kShiftPerWarp;
+    p.base_lo = base_lo;
+    p.base_hi = base_hi;
+    p.ph = (uint32_t)(lo0 & 3u);
+    p.k0 = r.key[0];
+    p.k1 = r.key[1];
+    constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 4
+                       : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64 ||
+                          V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64)
+                           ? 1
+                           : 2;
+    void (*k_uni)(const ShiftParams);
+    void (*k_carry)(const ShiftParams);
+    if constexpr (stream_wants_5_ctas<V>()) {
+      k_uni = philox_shift_kernel_5<V, kU, true>;
+      k_carry = philox_shift_kernel_5<V, kU, false>;
+    } else {
+      k_uni = philox_shift_kernel<V, kU, true>;
+      k_carry = philox_shift_kernel<V, kU, false>;
+    }
+    static std::atomic<int> occ[2] = {{0}, {0}};
+    int o = occ[0].load(std::memory_order_relaxed);
+    if (o == 0) {
+      o = blocks_per_sm(k_uni);
+      occ[0].store(o, std::memory_order_relaxed);
+      occ[1].store(blocks_per_sm(k_carry), std::memory_order_relaxed);
+    }
+    const int64_t warps = (p.chunks + kU - 1) / kU;
+    int64_t grid = (warps + (kThreads / 32) - 1) / (kThreads / 32);
+    if (grid < 1) grid = 1;
+    const int64_t cap = (int64_t)sms * o;
+    if (grid > cap) grid = cap;
+    // blocks touched: up to (chunks + kU * warps in flight) * 31 + 32 past base
+    const uint64_t reach = (uint64_t)(p.chunks + (int64_t)kU * grid * (kThreads / 32) + 1) *
+                               (uint64_t)kShiftPerWarp + 64u;
+    const bool hi_uniform = base_lo + reach >= base_lo;
+    if (!hi_uniform) {
+      const int64_t cap2 = (int64_t)sms * occ[1].load(std::memory_order_relaxed);
+      if (grid > cap2) grid = cap2;
+    }
+    (hi_uniform ? k_uni : k_carry)<<<(unsigned)grid, kThreads, 0, stream>>>(p);
   } else {
     StagedParams p;
     p.t = r.t;
