@@ -205,6 +205,27 @@ def test_icdf_f32_tails_and_sweep(g, kind, p0, p1):
     print(f"ICDF FP32 kind {kind}: worst error / max(1,|x|) = {worst:.3e}")
 
 
+@pytest.mark.parametrize("kind", [3, 5])
+@pytest.mark.parametrize("m,s", [(0.0, 1.0), (-2.0, 1.5), (1.0, 0.5), (85.5, 2.0**-30),
+                                 (86.5, 2.0**-30), (-85.5, 2.0**-30), (-86.5, 2.0**-30)])
+def test_fp32_lognormal_ranges(g, kind, m, s):
+    """FP32 lognormal (Box-Muller and inverse CDF) over parameters: the
+    library tolerance for moderate m + s z, and with s = 2^-30 (m + s z rounds
+    to m exactly in float) a relative bound of 2e-6 for results near the top
+    and the bottom of the normal float range."""
+    rng = np.random.Generator(np.random.PCG64(21))
+    n = 100001
+    nw = oracle.words_for(kind, 1, n)
+    w = rng.integers(0, 1 << 32, nw, dtype=np.uint64).astype(np.uint32)
+    got = _gpu(g, kind, 1, m, s, w, n)
+    ref = oracle.transform_words(kind, 1, m, s, n, w)
+    if s < 1e-6:
+        rel = np.abs(got.astype(np.float64) - ref) / np.abs(ref)
+        assert float(rel.max()) <= 2e-6, f"kind {kind} m={m}: worst relative {rel.max():.3e}"
+    else:
+        _check(kind, 1, got, ref, f"FP32 lognormal kind {kind} m={m} s={s}")
+
+
 @pytest.mark.parametrize("kind,p0,p1", [(4, 0.0, 1.0), (5, 0.0, 1.0)])
 def test_icdf_f32_all_2_23(g, kind, p0, p1):
     """All 2^23 FP32 inverse-CDF inputs u = (k + 1/2) 2^-23 (the 9 low word
