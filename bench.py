@@ -211,8 +211,8 @@ BM64_PRODUCTS_PER_PAIR = 42
 # current kernels: one launch of 2.68e8 samples scaled by 1e9 / 2.68e8
 # (profiles/gaussian_f64_2.68e8_full.md); replaced when a kernel changes.
 NCU_TRAFFIC_PER_1E9 = {
-    "mrg32k3a/gaussian_f64": (2.083409e9 + 0.790e6) / 0.268,
-    "philox4x32_10/gaussian_f64": (2.083185e9 + 0.450e6) / 0.268,
+    "mrg32k3a/gaussian_f64": (2.083029e9 + 0.160e6) / 0.268,
+    "philox4x32_10/gaussian_f64": (2.083297e9 + 1.154e6) / 0.268,
 }
 PRODUCTS_PER_SAMPLE = {
     "philox4x32_10/bits_u32": 5, "philox4x32_10/uniform_f32": 5,
