@@ -12,14 +12,15 @@
 //     its block boundary (and Box-Muller pairs do not straddle groups), group
 //     j is exactly Philox block base + j: one block, one transform, one
 //     st.v4.  Only the first and the last group of a stream may be partial.
-//   * shift kernel (one stream whose output starts on a unit boundary, any
-//     other word phase): group j is the tail of block base + j and the head
-//     of block base + j + 1; a warp computes 32 consecutive blocks and emits
-//     31 groups, exchanging the words between neighbouring lanes by shuffle.
-//   * staged kernel: the rest (substreams at another phase, a Box-Muller pair
-//     split by the output's start).  A CTA computes the blocks covering a
-//     tile of 256 groups into shared memory, then each thread assembles its
-//     group from the words it needs.
+//   * shift kernel (one stream at any other phase): group j is the tail of
+//     block base + j and the head of block base + j + 1; a warp computes 32
+//     consecutive blocks and emits 31 groups, exchanging the words between
+//     neighbouring lanes by shuffle.  When the output's start splits a
+//     Box-Muller pair, lanes transform pair-aligned groups one element
+//     earlier and exchange the straddling element too (30 groups per warp).
+//   * staged kernel: substreams at another phase.  A CTA computes the blocks
+//     covering a tile of 256 groups into shared memory, then each thread
+//     assembles its group from the words it needs.
 // Both write every output exactly once; results do not depend on the launch
 // geometry (each output is a function of its word index only).
 #include <cuda_runtime.h>
@@ -140,7 +141,14 @@ __global__ void __launch_bounds__(kThreads, 5) philox_stream_kernel_5(const Stre
 // computes 32 consecutive blocks and emits the 31 groups that start in its
 // lanes 0..30, taking the next block's words from lane + 1 by shuffle, so a
 // group still costs 32/31 of a block and no shared memory or barrier.  U
-// chunks of 31 groups per warp per iteration, as U blocks per thread above.
+// chunks of groups per warp per iteration, as U blocks per thread above.
+//
+// kSplit: the output's start splits a Box-Muller pair (odd head).  Lane l
+// then transforms the pair-aligned "virtual" group that starts one element
+// earlier (its words found as above, for any phase), and output group j is
+// virtual group j without its first element plus the first element of
+// virtual group j + 1, taken from lane + 1: 30 groups per warp, every pair
+// transformed once.
 struct ShiftParams {
   TransformParams t;
   uint4* gbase;       // 16-byte aligned address of group 0 (may precede out)
@@ -148,19 +156,23 @@ struct ShiftParams {
   int64_t n;          // elements
   int64_t head;       // elements of group 0 that lie before out
   int64_t groups;
-  int64_t chunks;     // ceil(groups / 31)
-  uint64_t base_lo;   // block holding the first word of group 0
+  int64_t chunks;     // ceil(groups / groups per warp chunk)
+  uint64_t base_lo;   // block holding the first word of (virtual) group 0
   uint64_t base_hi;
-  uint32_t ph;        // 1..3
+  uint32_t ph;        // its word phase: 1..3, or 0..3 with kSplit
   uint32_t k0, k1;
 };
 
-constexpr int kShiftPerWarp = 31;
+template <bool kSplit>
+__host__ __device__ constexpr int shift_per_warp() {
+  return kSplit ? 30 : 31;
+}
 
-template <int V, int U, bool kHiUniform>
+template <int V, int U, bool kHiUniform, bool kSplit>
 __device__ __forceinline__ void philox_shift_body(const ShiftParams& p) {
   using I = VInfo<V>;
   constexpr int kEpg = 16 / I::es;
+  constexpr int kPer = shift_per_warp<kSplit>();
   const int lane = threadIdx.x & 31;
   const int64_t TW = (int64_t)gridDim.x * (kThreads / 32);
   // the loop bound depends only on the warp: every shuffle has all 32 lanes
@@ -169,27 +181,37 @@ __device__ __forceinline__ void philox_shift_body(const ShiftParams& p) {
     uint4 b[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const uint64_t j = (uint64_t)((c + u * TW) * kShiftPerWarp + lane);
+      const uint64_t j = (uint64_t)((c + u * TW) * kPer + lane);
       const uint64_t lo = p.base_lo + j;
       const uint64_t hi = kHiUniform ? p.base_hi : p.base_hi + ((lo < p.base_lo) ? 1u : 0u);
       b[u] = philox4x32_10(ctr_from(lo, hi), p.k0, p.k1);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const uint32_t n0 = __shfl_down_sync(0xFFFFFFFFu, b[u].x, 1);
-      const uint32_t n1 = __shfl_down_sync(0xFFFFFFFFu, b[u].y, 1);
-      const uint32_t n2 = __shfl_down_sync(0xFFFFFFFFu, b[u].z, 1);
-      uint4 w;
-      if (p.ph == 1) {
-        w = make_uint4(b[u].y, b[u].z, b[u].w, n0);
-      } else if (p.ph == 2) {
-        w = make_uint4(b[u].z, b[u].w, n0, n1);
-      } else {
-        w = make_uint4(b[u].w, n0, n1, n2);
+      uint4 w = b[u];
+      if (!kSplit || p.ph != 0) {
+        const uint32_t n0 = __shfl_down_sync(0xFFFFFFFFu, b[u].x, 1);
+        const uint32_t n1 = __shfl_down_sync(0xFFFFFFFFu, b[u].y, 1);
+        const uint32_t n2 = __shfl_down_sync(0xFFFFFFFFu, b[u].z, 1);
+        if (p.ph == 1) {
+          w = make_uint4(b[u].y, b[u].z, b[u].w, n0);
+        } else if (p.ph == 2) {
+          w = make_uint4(b[u].z, b[u].w, n0, n1);
+        } else {
+          w = make_uint4(b[u].w, n0, n1, n2);
+        }
       }
-      const int64_t j = (c + u * TW) * kShiftPerWarp + lane;
-      if (lane < kShiftPerWarp && j < p.groups) {
-        const uint4 o = block_outputs<V>(w, p.t);
+      const int64_t j = (c + u * TW) * kPer + lane;
+      uint4 o;
+      if constexpr (kSplit) {
+        // every lane transforms its virtual group: lane l + 1's is needed by l
+        const uint4 v = block_outputs<V>(w, p.t);
+        const uint32_t m0 = __shfl_down_sync(0xFFFFFFFFu, v.x, 1);
+        const uint32_t m1 = __shfl_down_sync(0xFFFFFFFFu, v.y, 1);
+        o = I::es == 4 ? make_uint4(v.y, v.z, v.w, m0) : make_uint4(v.z, v.w, m0, m1);
+      }
+      if (lane < kPer && j < p.groups) {
+        if constexpr (!kSplit) o = block_outputs<V>(w, p.t);
         const int64_t e0 = j * kEpg - p.head;
         if (e0 >= 0 && e0 + kEpg <= p.n) {
           p.gbase[j] = o;
@@ -201,14 +223,14 @@ __device__ __forceinline__ void philox_shift_body(const ShiftParams& p) {
   }
 }
 
-template <int V, int U, bool kHiUniform>
+template <int V, int U, bool kHiUniform, bool kSplit>
 __global__ void __launch_bounds__(kThreads) philox_shift_kernel(const ShiftParams p) {
-  philox_shift_body<V, U, kHiUniform>(p);
+  philox_shift_body<V, U, kHiUniform, kSplit>(p);
 }
 
-template <int V, int U, bool kHiUniform>
+template <int V, int U, bool kHiUniform, bool kSplit>
 __global__ void __launch_bounds__(kThreads, 5) philox_shift_kernel_5(const ShiftParams p) {
-  philox_shift_body<V, U, kHiUniform>(p);
+  philox_shift_body<V, U, kHiUniform, kSplit>(p);
 }
 
 // ------------------------------------------------------------ substreams
@@ -355,6 +377,53 @@ int blocks_per_sm(K kernel) {
   return b;
 }
 
+// Launches the shift kernel: words of (virtual) group 0 start at word a of
+// the stream (128-bit, a = off - head words, one element earlier for kSplit).
+template <int V, bool kSplit>
+void launch_shift(const FillRequest& r, ShiftParams& p, uint64_t a_lo, uint64_t a_hi, int sms,
+                  cudaStream_t stream) {
+  constexpr int kPer = shift_per_warp<kSplit>();
+  constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 4
+                     : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64 ||
+                        V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64)
+                         ? 1
+                         : 2;
+  p.base_lo = (a_lo >> 2) | (a_hi << 62);
+  p.base_hi = a_hi >> 2;
+  p.ph = (uint32_t)(a_lo & 3u);
+  p.chunks = (p.groups + kPer - 1) / kPer;
+  void (*k_uni)(const ShiftParams);
+  void (*k_carry)(const ShiftParams);
+  if constexpr (stream_wants_5_ctas<V>()) {
+    k_uni = philox_shift_kernel_5<V, kU, true, kSplit>;
+    k_carry = philox_shift_kernel_5<V, kU, false, kSplit>;
+  } else {
+    k_uni = philox_shift_kernel<V, kU, true, kSplit>;
+    k_carry = philox_shift_kernel<V, kU, false, kSplit>;
+  }
+  static std::atomic<int> occ[2] = {{0}, {0}};
+  int o = occ[0].load(std::memory_order_relaxed);
+  if (o == 0) {
+    o = blocks_per_sm(k_uni);
+    occ[0].store(o, std::memory_order_relaxed);
+    occ[1].store(blocks_per_sm(k_carry), std::memory_order_relaxed);
+  }
+  const int64_t warps = (p.chunks + kU - 1) / kU;
+  int64_t grid = (warps + (kThreads / 32) - 1) / (kThreads / 32);
+  if (grid < 1) grid = 1;
+  const int64_t cap = (int64_t)sms * o;
+  if (grid > cap) grid = cap;
+  // blocks touched: below (chunks + kU * warps in flight) * kPer + 32 past base
+  const uint64_t reach =
+      (uint64_t)(p.chunks + (int64_t)kU * grid * (kThreads / 32) + 1) * (uint64_t)kPer + 64u;
+  const bool hi_uniform = p.base_lo + reach >= p.base_lo;
+  if (!hi_uniform) {
+    const int64_t cap2 = (int64_t)sms * occ[1].load(std::memory_order_relaxed);
+    if (grid > cap2) grid = cap2;
+  }
+  (hi_uniform ? k_uni : k_carry)<<<(unsigned)grid, kThreads, 0, stream>>>(p);
+}
+
 template <int V>
 grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
   using I = VInfo<V>;
@@ -458,8 +527,9 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.tqsb_lo = (uint64_t)tqsb;
     p.tqsb_hi = (uint64_t)(tqsb >> 64);
     philox_multi_kernel<V><<<(unsigned)grid, kThreads, 0, stream>>>(p);
-  } else if (r.num_streams == 1 && (phase_w % (uint32_t)I::wpu) == 0) {
-    // a word phase other than the pointer's, units not split by the start
+  } else if (r.num_streams == 1 &&
+             ((phase_w % (uint32_t)I::wpu) == 0 || (I::epu == 2 && (head & 1) != 0))) {
+    // one stream at another word phase, or a pair split by the output's start
     ShiftParams p;
     p.t = r.t;
     p.out = r.out;
@@ -467,47 +537,17 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.n = r.n;
     p.head = head;
     p.groups = groups;
-    p.chunks = (groups + kShiftPerWarp - 1) / kShiftPerWarp;
-    p.base_lo = base_lo;
-    p.base_hi = base_hi;
-    p.ph = (uint32_t)(lo0 & 3u);
     p.k0 = r.key[0];
     p.k1 = r.key[1];
-    constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 4
-                       : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64 ||
-                          V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64)
-                           ? 1
-                           : 2;
-    void (*k_uni)(const ShiftParams);
-    void (*k_carry)(const ShiftParams);
-    if constexpr (stream_wants_5_ctas<V>()) {
-      k_uni = philox_shift_kernel_5<V, kU, true>;
-      k_carry = philox_shift_kernel_5<V, kU, false>;
-    } else {
-      k_uni = philox_shift_kernel<V, kU, true>;
-      k_carry = philox_shift_kernel<V, kU, false>;
+    if ((phase_w % (uint32_t)I::wpu) == 0) {
+      launch_shift<V, false>(r, p, lo0, hi0, sms, stream);
+    } else if constexpr (I::epu == 2) {
+      // the virtual groups start one element (es / 4 words) earlier
+      const uint32_t pv = phase_w + (uint32_t)(I::es / 4);
+      const uint64_t a_lo = r.off_lo - pv;
+      const uint64_t a_hi = r.off_hi - ((r.off_lo < pv) ? 1u : 0u);
+      launch_shift<V, true>(r, p, a_lo, a_hi, sms, stream);
     }
-    static std::atomic<int> occ[2] = {{0}, {0}};
-    int o = occ[0].load(std::memory_order_relaxed);
-    if (o == 0) {
-      o = blocks_per_sm(k_uni);
-      occ[0].store(o, std::memory_order_relaxed);
-      occ[1].store(blocks_per_sm(k_carry), std::memory_order_relaxed);
-    }
-    const int64_t warps = (p.chunks + kU - 1) / kU;
-    int64_t grid = (warps + (kThreads / 32) - 1) / (kThreads / 32);
-    if (grid < 1) grid = 1;
-    const int64_t cap = (int64_t)sms * o;
-    if (grid > cap) grid = cap;
-    // blocks touched: up to (chunks + kU * warps in flight) * 31 + 32 past base
-    const uint64_t reach = (uint64_t)(p.chunks + (int64_t)kU * grid * (kThreads / 32) + 1) *
-                               (uint64_t)kShiftPerWarp + 64u;
-    const bool hi_uniform = base_lo + reach >= base_lo;
-    if (!hi_uniform) {
-      const int64_t cap2 = (int64_t)sms * occ[1].load(std::memory_order_relaxed);
-      if (grid > cap2) grid = cap2;
-    }
-    (hi_uniform ? k_uni : k_carry)<<<(unsigned)grid, kThreads, 0, stream>>>(p);
   } else {
     StagedParams p;
     p.t = r.t;
