@@ -383,7 +383,7 @@ template <int V, bool kSplit>
 void launch_shift(const FillRequest& r, ShiftParams& p, uint64_t a_lo, uint64_t a_hi, int sms,
                   cudaStream_t stream) {
   constexpr int kPer = shift_per_warp<kSplit>();
-  constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 4
+  constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 6
                      : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64 ||
                         V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64)
                          ? 1
@@ -471,7 +471,7 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     }
     p.jf = jf;
     p.jl = jl;
-    constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 4
+    constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 6
                        : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64 ||
                           V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64)
                            ? 1
