@@ -115,6 +115,19 @@ __device__ __forceinline__ void philox_stream_body(const StreamParams& p) {
     *dst = block_outputs<V>(group_block<V, kHiUniform>(p, (uint64_t)j), p.t);
 }
 
+// Counter blocks per thread per loop iteration: six for bits and the FP32
+// uniforms (2, 4, 6 and 8 measured: 6 fastest), two for the other FP32 and
+// the FP64 uniform transforms (3 and 4 slower), one for the FP64 fixed-point
+// transforms (hundreds of instructions per unit).
+template <int V>
+constexpr int blocks_per_thread() {
+  return (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 6
+         : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64 ||
+            V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64)
+             ? 1
+             : 2;
+}
+
 // The Box-Muller and FP32 inverse-CDF variants gain from a fifth resident CTA
 // per SM (registers capped near 51: 1-5 % faster); the light variants keep
 // the compiler's own register choice, which a CTA minimum would change.
@@ -383,11 +396,7 @@ template <int V, bool kSplit>
 void launch_shift(const FillRequest& r, ShiftParams& p, uint64_t a_lo, uint64_t a_hi, int sms,
                   cudaStream_t stream) {
   constexpr int kPer = shift_per_warp<kSplit>();
-  constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 6
-                     : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64 ||
-                        V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64)
-                         ? 1
-                         : 2;
+  constexpr int kU = blocks_per_thread<V>();
   p.base_lo = (a_lo >> 2) | (a_hi << 62);
   p.base_hi = a_hi >> 2;
   p.ph = (uint32_t)(a_lo & 3u);
@@ -471,11 +480,7 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     }
     p.jf = jf;
     p.jl = jl;
-    constexpr int kU = (V == V_BITS || V == V_U01_F32 || V == V_UNI_F32) ? 6
-                       : (V == V_GAUSS_F64 || V == V_LOGN_F64 || V == V_STDGAUSS_F64 ||
-                          V == V_ICDF_GAUSS_F64 || V == V_ICDF_LOGN_F64)
-                           ? 1
-                           : 2;
+    constexpr int kU = blocks_per_thread<V>();
     const bool hi_uniform = base_lo + (uint64_t)groups >= base_lo;  // no carry into the top half
     void (*kernel)(const StreamParams);
     if constexpr (stream_wants_5_ctas<V>()) {
