@@ -286,6 +286,54 @@ def run_extra(grng, torch, dev, n, buf, stream, reps, hbm_peak):
     return out
 
 
+def run_tts(grng, torch, dev, stream, with_curand, sizes=(10**3, 10**6, 10**8), reps=7):
+    """Time to solution of one call, as the paper's RNG burner counts it
+    (Sec. 6): engine or generator creation, seeding, one fill of n FP32
+    uniforms on [0,1) and a stream synchronisation, host wall clock, median of
+    reps after one untimed call; ours against cuRAND's host API (create, seed,
+    set stream, generate, sync, destroy), both engines."""
+    out = torch.empty(max(sizes), dtype=torch.float32, device=dev)
+    cr = None
+    if with_curand:
+        try:
+            cr = Curand()
+        except Exception:  # noqa: BLE001
+            cr = None
+    d = grng.Distribution.uniform(0.0, 1.0)
+    res = {}
+    for ek, en in ENGINES:
+        res[en] = {}
+        for n in sizes:
+            def ours():
+                e = grng.Engine(ek, W.SWEEP_SEED, 0)
+                grng.generate(d, e, out, n=n, stream=stream)
+                stream.synchronize()
+
+            def theirs():
+                g = cr.generator(ek, W.SWEEP_SEED, stream.cuda_stream)
+                cr.fill(g, "uniform_f32", out.data_ptr(), n)
+                stream.synchronize()
+                cr.destroy(g)
+
+            row = {}
+            for key, fn in (("ours_us", ours), ("curand_us", theirs if cr else None)):
+                if fn is None:
+                    continue
+                fn()
+                ts = []
+                for _ in range(reps):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    fn()
+                    ts.append(time.perf_counter() - t0)
+                row[key] = round(statistics.median(ts) * 1e6, 1)
+            if "curand_us" in row:
+                row["speedup_ours"] = round(row["curand_us"] / row["ours_us"], 2)
+            res[en][str(n)] = row
+    return {"how": "create + seed + one FP32 uniform fill of n + stream sync, host wall clock, "
+                   f"median of {reps}", **res}
+
+
 def run_batched(grng, torch, dev, reps):
     """Batched requests: 4096 Philox engines (seeds 1..4096), log-uniform sizes in
     [64, 2^20], five distributions; one graph-replayed persistent launch vs
@@ -633,6 +681,10 @@ def run_ours(args):
         except Exception as ex:  # noqa: BLE001
             curand = {"unavailable": str(ex)[:200]}
 
+    tts = None
+    if rank == 0 and not args.skip_tts:
+        tts = run_tts(grng, torch, dev, stream, not args.skip_curand)
+
     # end to end through the C ABI with host buffers (generate + D2H per chunk)
     e2e = None
     if not args.skip_e2e:
@@ -725,7 +777,7 @@ def run_ours(args):
                                           "gsamples_s": target["gsamples_s"]},
             "ceilings": {"hbm_copy_gbs": hbm_peak, "write_only_gbs": round(write_gbs, 1),
                          "products_per_s": mul_rate, "products_per_s_probe": mul_probe},
-            "per_kernel": per_kernel, "curand": curand, "other_fills": extra,
+            "per_kernel": per_kernel, "curand": curand, "tts": tts, "other_fills": extra,
             "batched": batched, "serving": serving,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": args.steps * len(cases)}
@@ -753,6 +805,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-tts", action="store_true",
+                    help="skip the time-to-solution calls (create + seed + fill + sync)")
     ap.add_argument("--skip-extra", action="store_true",
                     help="skip the fills outside the sweep (inverse CDF, FP64 lognormal, ...)")
     ap.add_argument("--batch-reps", type=int, default=20)
