@@ -72,7 +72,9 @@ GRNG_BM_HD uint64_t neg_icdf(uint64_t m1) {
   const int32_t b7 = (int32_t)coef(base + 7) +
                      (int32_t)(((int64_t)(int32_t)coef(base + 8) * s31) >> 31);
   int64_t b = coef(base + 6) + (((int64_t)b7 * s31) >> 31);
+#if defined(__CUDA_ARCH__)
 #pragma unroll
+#endif
   for (int i = 5; i >= 0; --i) b = coef(base + i) + mulhi_su(b, S);
   return b > 0 ? (uint64_t)b : 0ull;
 }

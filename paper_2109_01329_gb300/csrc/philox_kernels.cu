@@ -393,7 +393,7 @@ int blocks_per_sm(K kernel) {
 // Launches the shift kernel: words of (virtual) group 0 start at word a of
 // the stream (128-bit, a = off - head words, one element earlier for kSplit).
 template <int V, bool kSplit>
-void launch_shift(const FillRequest& r, ShiftParams& p, uint64_t a_lo, uint64_t a_hi, int sms,
+void launch_shift(ShiftParams& p, uint64_t a_lo, uint64_t a_hi, int sms,
                   cudaStream_t stream) {
   constexpr int kPer = shift_per_warp<kSplit>();
   constexpr int kU = blocks_per_thread<V>();
@@ -545,13 +545,13 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.k0 = r.key[0];
     p.k1 = r.key[1];
     if ((phase_w % (uint32_t)I::wpu) == 0) {
-      launch_shift<V, false>(r, p, lo0, hi0, sms, stream);
+      launch_shift<V, false>(p, lo0, hi0, sms, stream);
     } else if constexpr (I::epu == 2) {
       // the virtual groups start one element (es / 4 words) earlier
       const uint32_t pv = phase_w + (uint32_t)(I::es / 4);
       const uint64_t a_lo = r.off_lo - pv;
       const uint64_t a_hi = r.off_hi - ((r.off_lo < pv) ? 1u : 0u);
-      launch_shift<V, true>(r, p, a_lo, a_hi, sms, stream);
+      launch_shift<V, true>(p, a_lo, a_hi, sms, stream);
     }
   } else {
     StagedParams p;
