@@ -9,7 +9,7 @@ advance the engine.  value = samples of all ranks / step time (Gsamples/s).
 
 Beside it: per-kernel achieved HBM write GB/s against the measured copy peak,
 the roofline of the dominant kernel, cuRAND's host API on the same fills
-(the native baseline of the paper, Sec. 3.2), an end-to-end number through
+(the native baseline of the paper, Sec. 4.2), an end-to-end number through
 the C ABI with host buffers (generate + device-to-host copy), clocks sampled
 during the timed region, and the CPU oracle as the timed CPU baseline.
 
@@ -288,7 +288,7 @@ def run_extra(grng, torch, dev, n, buf, stream, reps, hbm_peak):
 
 def run_tts(grng, torch, dev, stream, with_curand, sizes=(10**3, 10**6, 10**8), reps=7):
     """Time to solution of one call, as the paper's RNG burner counts it
-    (Sec. 6): engine or generator creation, seeding, one fill of n FP32
+    (Sec. 7): engine or generator creation, seeding, one fill of n FP32
     uniforms on [0,1) and a stream synchronisation, host wall clock, median of
     reps after one untimed call; ours against cuRAND's host API (create, seed,
     set stream, generate, sync, destroy), both engines."""

@@ -2,12 +2,12 @@
  * grng.h - C ABI of a GB300 (sm_103a) bulk random number library.
  *
  * The interface follows the engine / distribution / generate shape of the
- * oneMKL RNG domain that the paper extends (Sec. 3.1: engine classes with
+ * oneMKL RNG domain that the paper extends (Sec. 4.1: engine classes with
  * `generate` templates parameterised by a distribution object that carries
  * its own parameters and a custom range), and the native generator flow of
- * Sec. 3.2 (create a generator, set seed and offset, generate into device
- * memory, destroy).  The paper's generate(distr, n, r) call (Sec. 3.3,
- * Listing 1) followed by a separate range-transform kernel (Sec. 3.3,
+ * Sec. 4.2 (create a generator, set seed and offset, generate into device
+ * memory, destroy).  The paper's generate(distr, n, r) call (Sec. 4.3,
+ * Listing 1) followed by a separate range-transform kernel (Sec. 4.3,
  * Listing 2) becomes one call and one kernel here: the transform is fused
  * into the generator.
  *
@@ -30,7 +30,7 @@
  * (seed mod 2^32, seed >> 32); word g is lane (g mod 4) of the block whose
  * 128-bit counter is floor(g / 4).  MRG32k3a (L'Ecuyer 1999): seeded state
  * x1 = (1, 1, seed mod m1), x2 = (1, 1, 1); word n is (x1_n - x2_n) mod m1.
- * The paper names both engines (Sec. 3.1) but defines neither.  Offsets
+ * The paper names both engines (Sec. 4.1) but defines neither.  Offsets
  * are taken mod 2^128: for Philox word 2^128 + g is word g; an MRG32k3a fill
  * whose words cross 2^128 within one call continues its recursion, and the
  * engine's next offset is reduced mod 2^128.
@@ -84,12 +84,12 @@ typedef enum grng_dist_kind {
 typedef enum grng_dtype { GRNG_U32 = 0, GRNG_F32 = 1, GRNG_F64 = 2 } grng_dtype;
 
 /*
- * A distribution with its parameters (Sec. 3.1: distribution objects carry
+ * A distribution with its parameters (Sec. 4.1: distribution objects carry
  * mean / standard deviation or a custom range).  For F32 outputs the
  * parameters are first rounded to float.
  *   uniform:  u = (w >> 8) 2^-24 (F32) or ((w_a << 32 | w_b) >> 11) 2^-53
  *             (F64); r = a + (b - a) u with round-to-nearest multiply and add
- *             and no fused multiply-add (the range transform of Sec. 3.3,
+ *             and no fused multiply-add (the range transform of Sec. 4.3,
  *             Listing 2); r >= b is replaced by the largest value below b.
  *             Requires finite a < b with b - a finite in the output type.
  *   gaussian: pair k -> u1 in (0, 1] from its first unit, u2 in [0, 1) from its
@@ -97,7 +97,7 @@ typedef enum grng_dtype { GRNG_U32 = 0, GRNG_F32 = 1, GRNG_F64 = 2 } grng_dtype;
  *             rho = sqrt(-2 ln u1); output mean + stddev z.
  *   lognormal: exp(m + s z) with z as for gaussian.
  *   gaussian / lognormal ICDF (oneMKL's icdf method, which cuRAND offers
- *             only for quasi-random generators, Sec. 3.1): one uniform per
+ *             only for quasi-random generators, Sec. 4.1): one uniform per
  *             output, u = (k + 1/2) 2^-23 with k = w >> 9 (F32) or
  *             u = (x + 1/2) 2^-52 with x = ((w_a << 32 | w_b) >> 12) (F64),
  *             z = Phi^-1(u) (F32: x P(-log2(1 - x^2)) with x = 2u - 1, two
@@ -128,16 +128,20 @@ typedef struct grng_engine_state {
 typedef struct grng_engine* grng_engine_t;
 typedef struct CUstream_st* grng_stream_t; /* same type as cudaStream_t */
 
-/* Human-readable name of a status code (static storage; never NULL). */
+/* Human-readable name of a status code (static storage; never NULL).  The
+ * paper's generate wraps each native call in a status check (Sec. 4.3,
+ * Listing 1: CURAND_CALL and CUDA_CALL take a status variable); here every
+ * entry point returns that status instead. */
 GRNG_API const char* grng_status_string(grng_status status);
 
 /* Detail of the last error raised on the calling thread (static per-thread
- * storage, overwritten by the next failing call; "" if none). */
+ * storage, overwritten by the next failing call; "" if none).  A reading,
+ * not in the paper: the text behind a failing status of Sec. 4.3's calls. */
 GRNG_API const char* grng_last_error(void);
 
 /*
  * Creates an engine of `kind` seeded with `seed`, positioned at word offset
- * `offset` (Sec. 3.2: create the generator, then set seed and offset).
+ * `offset` (Sec. 4.2: create the generator, then set seed and offset).
  * *out receives the handle; release it with grng_engine_destroy.
  * Errors: INVALID_ARG (out NULL, bad kind), OOM.
  */
@@ -145,7 +149,7 @@ GRNG_API grng_status grng_engine_create(grng_engine_t* out, int32_t kind, uint64
 
 /*
  * Creates an engine from a seed initializer list of `count` (1..6) 32-bit
- * words (oneMKL engines accept such lists; cuRAND's do not, Sec. 3.1):
+ * words (oneMKL engines accept such lists; cuRAND's do not, Sec. 4.1):
  *   Philox4x32-10: words 0, 1 = key (k0, k1); words 2..5 = the starting
  *     128-bit block counter (c0..c3; missing words 0), i.e. word offset
  *     4 * counter (mod 2^128) + offset.  {lo, hi} equals seed lo + 2^32 hi.
@@ -161,20 +165,31 @@ GRNG_API grng_status grng_engine_create_words(grng_engine_t* out, int32_t kind,
 GRNG_API grng_status grng_engine_restore(grng_engine_t* out, const grng_engine_state* state);
 
 /* Copies an engine (same kind, seed and offset; independent afterwards).
- * oneMKL engines are copy-constructible (Sec. 3.1), cuRAND's are not. */
+ * oneMKL engines are copy-constructible (Sec. 4.1), cuRAND's are not. */
 GRNG_API grng_status grng_engine_copy(grng_engine_t* out, grng_engine_t src);
 
 /* Advances the engine by n = n_lo + 2^64 n_hi words (mod 2^128).  The next
- * generate call starts at the new offset. */
+ * generate call starts at the new offset.  Sec. 4.2 sets the offset as a
+ * generator option at creation; this sets it later, by the same rule (a
+ * reading: the unit of the offset is a 32-bit word).
+ * Errors: INVALID_ARG (NULL engine). */
 GRNG_API grng_status grng_engine_skip_ahead(grng_engine_t engine, uint64_t n_lo, uint64_t n_hi);
 
-/* Writes the engine's kind, seed and 128-bit word offset to *out. */
+/* Writes the engine's kind, seed, seed words and 128-bit word offset to *out
+ * (checkpoint / resume; grng_engine_restore reads it back).  The state is
+ * what Sec. 4.2's generator options set (seed, offset); saving it is a
+ * reading, not in the paper.  Errors: INVALID_ARG (NULL engine or out). */
 GRNG_API grng_status grng_engine_get_state(grng_engine_t engine, grng_engine_state* out);
 
-/* Releases an engine.  NULL is accepted and ignored. */
+/* Releases an engine (Sec. 4.2, step 5: the generator's destructor).  NULL
+ * is accepted and ignored. */
 GRNG_API grng_status grng_engine_destroy(grng_engine_t engine);
 
-/* Number of words that n outputs of `dist` consume (written to *words_out). */
+/* Number of words that n outputs of `dist` consume (written to *words_out):
+ * the consumption rule above.  A reading, not in the paper, which fixes no
+ * rule; shard boundaries and continuation offsets are computed from it.
+ * Errors: INVALID_ARG (NULL dist or words_out, bad kind / dtype pairing,
+ * bad parameters, n < 0), UNSUPPORTED (n > 2^40). */
 GRNG_API grng_status grng_words_for(const grng_distribution* dist, int64_t n, uint64_t* words_out);
 
 /*
@@ -211,8 +226,8 @@ GRNG_API grng_status grng_generate_substreams(const grng_distribution* dist, grn
 /*
  * Applies `dist` to caller-supplied words: dev_out[0 .. n) receives the n
  * outputs that grng_generate would produce from the word sequence
- * dev_words[0 .. grng_words_for(dist, n)) (the transform of Sec. 3.3,
- * Listing 2 and of the distribution objects of Sec. 3.1, without an engine).
+ * dev_words[0 .. grng_words_for(dist, n)) (the transform of Sec. 4.3,
+ * Listing 2 and of the distribution objects of Sec. 4.1, without an engine).
  * For bit sources other than the two engines, and for checking the
  * transforms on chosen inputs.  dev_words: device memory, 4-byte aligned,
  * owned by the caller.  Same errors as grng_generate (no engine involved).
@@ -221,7 +236,7 @@ GRNG_API grng_status grng_transform_words(const grng_distribution* dist, const u
                                           int64_t n, void* dev_out, grng_stream_t stream);
 
 /*
- * The RNG-burner flow of Sec. 4.1 / Sec. 6 (generate, then copy the output
+ * The RNG-burner flow of Sec. 5.1 / Sec. 7 (generate, then copy the output
  * to the host): fills host_ptr[0 .. n) like grng_generate, staging through
  * the caller's device buffer dev_work of work_bytes bytes (at least 2 MiB,
  * 256-byte aligned), chunk by chunk, copying each chunk device-to-host on
@@ -237,8 +252,8 @@ GRNG_API grng_status grng_generate_host(const grng_distribution* dist, grng_engi
 
 /* ------------------------------------------------------------------ batches
  * Many independent requests in one persistent launch: the event batching the
- * paper names as future work for FastCaloSim (Sec. 6), where per-call
- * overheads dominate small batches (Sec. 6, Figs. 2-4).  Requests of one
+ * paper names as future work for FastCaloSim (Sec. 7), where per-call
+ * overheads dominate small batches (Sec. 7, Figs. 2-4).  Requests of one
  * engine follow each other in its sequence in table order, exactly as the
  * same grng_generate calls would.  Engine state for the batch lives on the
  * device: every launch fills every request from its current device offset
@@ -291,8 +306,8 @@ GRNG_API grng_status grng_batch_commit(grng_batch_t batch, grng_stream_t stream)
 GRNG_API grng_status grng_batch_destroy(grng_batch_t batch);
 
 /* ------------------------------------------------------------------ serving
- * A continuous-batching server for FastCaloSim-shaped demand (Sec. 4.2: each
- * event needs three uniforms per calorimeter hit, thousands of hits; Sec. 6
+ * A continuous-batching server for FastCaloSim-shaped demand (Sec. 5.2: each
+ * event needs three uniforms per calorimeter hit, thousands of hits; Sec. 7
  * names event batching as the way to use the GPU).  Requests arrive at any
  * time; a scheduler thread admits them in arrival order while their outputs
  * fit a device-memory budget, packs the admitted ones into one batched
@@ -394,14 +409,17 @@ GRNG_API grng_status grng_server_destroy(grng_server_t server);
  *   requests return GRNG_ERR_UNSUPPORTED (split them into several calls; the
  *   engine continues its sequence across calls).
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress, with that device current); make that first call
- *   before any stream capture begins.
+ *   (cudaGetSymbolAddress, with that device current) and keeps it; make that
+ *   first call before any stream capture begins.  Do not use this function
+ *   on a device after cudaDeviceReset in the same process: the kept address
+ *   would be stale.
  *   All calls share the one array.  The library serialises its own calls
  *   and waits for each copy, so calls from one process do not overlap on the
  *   GPU; calls that did overlap would race on the array.  Nothing in it has
  *   to start at zero: every element copied out is written first.
- * Errors: as grng_generate; UNSUPPORTED above the size limit; CUDA if the
- * copy fails (the engine is then moved back to where it was).
+ * Errors: as grng_generate; UNSUPPORTED above the size limit or for a
+ * device ordinal of 256 or more; CUDA if the copy fails (the engine is then
+ * moved back to where it was).
  */
 GRNG_API grng_status grng_generate_host_static(const grng_distribution* dist,
                                                grng_engine_t engine, int64_t n,

@@ -8,10 +8,10 @@
 // the published definitions.
 //
 // What the paper fixes and what it leaves open:
-//   * Sec. 3.1 names the two engine families (Philox4x32x10 and an MRG) and
+//   * Sec. 4.1 names the two engine families (Philox4x32x10 and an MRG) and
 //     the oneMKL engine / distribution / generate(distr, engine, n, r)
-//     interface; Sec. 3.2 names seed and offset as generator options.
-//   * Sec. 3.3, Listing 2 gives the range transform r * (b - a) + a.
+//     interface; Sec. 4.2 names seed and offset as generator options.
+//   * Sec. 4.3, Listing 2 gives the range transform r * (b - a) + a.
 //   * Everything else (the generator definitions, seeding, word -> float
 //     conversion, Box-Muller pairing) is not in the paper.  The readings taken
 //     here are:
@@ -30,7 +30,7 @@
 //         uniform, u2 the [0,1) uniform of the second; z0 = rho cos(2 pi u2),
 //         z1 = rho sin(2 pi u2), rho = sqrt(-2 ln u1); gaussian = mean + sd z,
 //         lognormal = exp(m + s z).  An odd n still consumes the last pair.
-//       - ICDF method (oneMKL's icdf gaussian / lognormal, Sec. 3.1): one
+//       - ICDF method (oneMKL's icdf gaussian / lognormal, Sec. 4.1): one
 //         open-interval uniform per output, u = (k + 1/2) 2^-23, k = w >> 9
 //         (FP32) or u = (x + 1/2) 2^-52, x = ((w_a << 32 | w_b) >> 12) (FP64);
 //         z = Phi^-1(u), found by bisection and Newton steps on
@@ -270,7 +270,7 @@ double u01_f64_open0(uint32_t wa, uint32_t wb) {
   return std::ldexp((double)(x + 1u), -53);
 }
 
-// Range transform of Sec. 3.3, Listing 2, made exact: each operation is a
+// Range transform of Sec. 4.3, Listing 2, made exact: each operation is a
 // separate rounded float operation (the file is compiled without
 // contraction), and a result that rounds up to b is moved below b.
 float range_f32(float u, float a, float b) {
@@ -300,7 +300,7 @@ void box_muller_ld(long double u1, long double u2, long double* z0, long double*
 
 // ---------------------------------------------------------------- ICDF
 // Inverse-CDF method (oneMKL's icdf method of its gaussian / lognormal
-// distributions, Sec. 3.1): z = Phi^-1(u) for one open-interval uniform per
+// distributions, Sec. 4.1): z = Phi^-1(u) for one open-interval uniform per
 // output.  Reading: u = (k + 1/2) 2^-23 with k = w >> 9 (FP32) and
 // u = (x + 1/2) 2^-52 with x = ((w_a << 32 | w_b) >> 12) (FP64), exact
 // midpoints in (0, 1) symmetric about 1/2.
@@ -534,7 +534,7 @@ int oracle_generate(int engine, uint64_t seed, uint64_t off_lo, uint64_t off_hi,
 }
 
 // The whole path for an engine seeded by a list of 1..6 32-bit words
-// (oneMKL's seed initializer lists, Sec. 3.1).  Reading: Philox key = words
+// (oneMKL's seed initializer lists, Sec. 4.1).  Reading: Philox key = words
 // 0, 1 and starting block counter = words 2..5 (word offset 4 counter + off);
 // MRG32k3a x1_{-1}, x1_{-2}, x1_{-3} = words 0..2 (mod m1) and x2_{-1},
 // x2_{-2}, x2_{-3} = words 3..5 (mod m2), missing words 1.

@@ -378,6 +378,10 @@ def generate_host(dist: Distribution, engine: Engine, host_out, work, stream=Non
                                                                                  dist.dtype):
         raise ValueError("host_out must be a contiguous CPU tensor of the distribution's dtype")
     n = host_out.numel() if n is None else n
+    if n < 0 or n > host_out.numel():
+        raise ValueError(f"n = {n} outside [0, host_out.numel() = {host_out.numel()}]")
+    if not work.is_cuda:
+        raise ValueError("work must be a CUDA tensor")
     d = dist._c()
     nbytes = work.numel() * work.element_size()
     with torch.cuda.device(work.device):
@@ -389,7 +393,19 @@ def generate_host(dist: Distribution, engine: Engine, host_out, work, stream=Non
     return host_out
 
 
-STATIC_STAGE_BYTES = 64 << 20  # GRNG_STATIC_STAGE_BYTES
+def _header_stage_bytes() -> int:
+    """GRNG_STATIC_STAGE_BYTES as include/grng.h defines it (one source of truth)."""
+    import re
+
+    path = os.path.join(os.path.dirname(HERE), "include", "grng.h")
+    with open(path) as f:
+        m = re.search(r"#define\s+GRNG_STATIC_STAGE_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", f.read())
+    if m is None:
+        raise RuntimeError("GRNG_STATIC_STAGE_BYTES not found in include/grng.h")
+    return int(m.group(1)) << int(m.group(2))
+
+
+STATIC_STAGE_BYTES = _header_stage_bytes()
 
 
 def generate_host_static(dist: Distribution, engine: Engine, host_out, n: int | None = None,
@@ -403,6 +419,8 @@ def generate_host_static(dist: Distribution, engine: Engine, host_out, n: int | 
                                                                                  dist.dtype):
         raise ValueError("host_out must be a contiguous CPU tensor of the distribution's dtype")
     n = host_out.numel() if n is None else n
+    if n < 0 or n > host_out.numel():
+        raise ValueError(f"n = {n} outside [0, host_out.numel() = {host_out.numel()}]")
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
     d = dist._c()
     with torch.cuda.device(dev):

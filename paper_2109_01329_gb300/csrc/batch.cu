@@ -1,6 +1,6 @@
 // Batched generation: many independent Philox requests in one persistent
-// launch (the event batching the paper leaves as future work, Sec. 6, and the
-// small-batch latency it measures, Sec. 6 / Fig. 2-4).
+// launch (the event batching the paper leaves as future work, Sec. 7, and the
+// small-batch latency it measures, Sec. 7 / Fig. 2-4).
 //
 // A batch is planned once on the host (grng_batch_create): per request its
 // variant, parameters, output pointer, 16-byte group count and starting word

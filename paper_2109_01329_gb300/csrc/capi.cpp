@@ -3,8 +3,8 @@
 // variant, offset bookkeeping and the chunked generate-to-host flow.
 //
 // The engine object mirrors the generator of the paper's native flow
-// (Sec. 3.2: create, set seed and offset, generate, destroy) and oneMKL's
-// engine classes (Sec. 3.1), whose sequences continue across generate calls.
+// (Sec. 4.2: create, set seed and offset, generate, destroy) and oneMKL's
+// engine classes (Sec. 4.1), whose sequences continue across generate calls.
 #include <cuda_runtime.h>
 
 #include <cmath>

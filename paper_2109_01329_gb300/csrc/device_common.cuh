@@ -103,7 +103,7 @@ __device__ __forceinline__ double u01_f64(uint32_t wa, uint32_t wb) {
 }
 
 // ---------------------------------------------------------- range transform
-// Sec. 3.3, Listing 2 computes acc * (b - a) + a in a second kernel; here it
+// Sec. 4.3, Listing 2 computes acc * (b - a) + a in a second kernel; here it
 // is fused, with explicit round-to-nearest multiply and add (never
 // contracted into an FMA) and the half-open interval enforced.
 __device__ __forceinline__ float range_f32(float u, const TransformParams& t) {

@@ -1,6 +1,6 @@
 // MRG32k3a fill kernels with the distribution transform fused in.
 //
-// MRG32k3a (L'Ecuyer 1999; the paper's "MRG-based generators", Sec. 3.1) is a
+// MRG32k3a (L'Ecuyer 1999; the paper's "MRG-based generators", Sec. 4.1) is a
 // sequential recursion, so the output is cut into per-thread chunks of
 // consecutive units.  Each thread
 //   1. jumps the call's starting state to its chunk with the compile-time

@@ -3,7 +3,7 @@
 // both the host (engine offsets) and the device (per-thread jumps).
 //
 // MRG32k3a (L'Ecuyer 1999) is the "MRG-based generator" family the paper's
-// library offers beside Philox (Sec. 3.1).  State vectors are
+// library offers beside Philox (Sec. 4.1).  State vectors are
 // (x_{n-3}, x_{n-2}, x_{n-1}); one step is multiplication by the companion
 // matrix A of the recursion.  A jump by k steps multiplies by A^k, built from
 // the binary expansion of k with the powers A^(2^j) tabulated here.

@@ -2,7 +2,7 @@
 //
 // The paper's path is two kernels: the vendor generator writes raw uniforms,
 // then a SYCL kernel re-reads and rewrites the buffer to apply the range
-// (Sec. 3.3, Listings 1 and 2; profiled as separate kernels in Sec. 6, Fig. 4).
+// (Sec. 4.3, Listings 1 and 2; profiled as separate kernels in Sec. 7, Fig. 4).
 // Here one kernel computes each counter block in registers, transforms it and
 // stores it once: 4 output bytes per word and no reads.
 //

@@ -1,8 +1,8 @@
 // Continuous-batching server for generation requests (grng_server_*).
 //
-// FastCaloSim (Sec. 4.2) asks for random numbers event by event: three
+// FastCaloSim (Sec. 5.2) asks for random numbers event by event: three
 // uniforms per calorimeter hit and thousands of hits per event, with event
-// batching named as the way to use the GPU better (Sec. 6).  The server takes
+// batching named as the way to use the GPU better (Sec. 7).  The server takes
 // such requests as they arrive and keeps the GPU busy with them:
 //   * submit() queues a request (up to four distribution parts drawn in turn
 //     from one Philox4x32-10 engine given by seed and offset) and returns at

@@ -16,7 +16,10 @@
 // before returning, so two calls never overlap on the GPU within one
 // process.  Calls that did overlap on the GPU would race on the array.
 // Nothing in the array has to start at zero: a call writes every element it
-// copies out before copying it.
+// copies out before copying it.  The array's device address is looked up
+// once per device and kept; after cudaDeviceReset the module is loaded anew
+// at another address, so the entry point must not be used on a device that
+// was reset in the same process.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -66,10 +69,15 @@ extern "C" grng_status grng_generate_host_static(const grng_distribution* dist,
   std::lock_guard<std::mutex> lock(g_static_mutex);
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
-  if (err != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (err != cudaSuccess) {
     set_error("cudaGetDevice failed: %s", cudaGetErrorString(err));
     cudaGetLastError();
     return GRNG_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device ordinal %d is outside the %d devices this entry point supports", dev,
+              kMaxDevices);
+    return GRNG_ERR_UNSUPPORTED;
   }
   // Set-up, once per device, with that device current: the host-side name
   // g_static_stage is only a stand-in, the kernel needs the device address.

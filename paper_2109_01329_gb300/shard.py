@@ -5,12 +5,13 @@ rank r of `world` writes elements [start, start + count) from word offset
 base + words_for(start), and the concatenation over ranks equals the
 unsharded fill bit for bit.  Boundaries fall on multiples of 4 elements, so
 they are whole Box-Muller pairs and (for 16-byte aligned buffers) 16-byte
-boundaries.
+boundaries.  The word offset comes from the library's consumption rule
+(grng_words_for), not from a copy of it here.
 """
 
 from __future__ import annotations
 
-_WPO = {0: 1, 1: 1, 2: 2}  # words per output by dtype (U32, F32, F64)
+from . import _binding
 
 
 def _boundary(r: int, world: int, n: int) -> int:
@@ -26,6 +27,7 @@ def shard_range(rank: int, world: int, n: int, kind: int, dtype: int):
         raise ValueError("bad rank / world / n")
     start = _boundary(rank, world, n)
     stop = _boundary(rank + 1, world, n)
-    # start is a multiple of 4, hence of a Box-Muller pair: words_for(start)
-    # is simply start words per output.
-    return start, stop - start, start * _WPO[dtype]
+    # (0, 1) are valid parameters of every distribution; the word count
+    # depends only on the kind, the dtype and the element count
+    dist = _binding.Distribution(kind, dtype, 0.0, 1.0)
+    return start, stop - start, _binding.words_for(dist, start)

@@ -5,11 +5,11 @@ distribution parameters.  This module produces those, for the tests (which
 feed them to both the CUDA library and the oracle) and for bench.py.  It holds
 none of the generators' or transforms' arithmetic.
 
-* Single-stream fills: the RNG-burner batches of Sec. 4.1 / Sec. 6 (Philox FP32
+* Single-stream fills: the RNG-burner batches of Sec. 5.1 / Sec. 7 (Philox FP32
   uniform, batch sizes up to 10^8), widened to 10^9 and to both engines and
   all distributions.
 * Substreams: 16384 MRG32k3a substreams 2^76 words apart (Philox: 2^40).
-* Batched requests and FastCaloSim-shaped demand (Sec. 4.2: three uniforms per
+* Batched requests and FastCaloSim-shaped demand (Sec. 5.2: three uniforms per
   calorimeter hit, thousands of hits per event) for the batched and served
   forms.
 """

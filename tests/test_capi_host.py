@@ -189,3 +189,39 @@ def test_seed_words_engines(g):
     assert lib.grng_engine_create_words(ctypes.byref(h), g.MRG32K3A, zeros, 7, 0) == 1
     m = (ctypes.c_uint32 * 1)(4294967087)  # m1 = 0 mod m1
     assert lib.grng_engine_create_words(ctypes.byref(h), g.MRG32K3A, m, 1, 0) == 0  # (1, 1, 0) is fine
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("words", [1, 6, 2**33 + 5, 2**70 + 3])
+def test_skip_back_by_wrapping_restores_the_state(g, kind, words):
+    """Moving an engine back by w words as a skip of 2^128 - w (the rollback of
+    grng_generate_host_static after a failed copy) restores its state exactly,
+    for word-seeded MRG32k3a engines too."""
+    engines = [g.Engine(kind, 2021, 11)]
+    if kind == 1:
+        engines.append(g.Engine.from_words(kind, [5, 6, 7, 8, 9, 10], 11))
+    for e in engines:
+        before = e.full_state
+        e.skip_ahead(words)
+        assert e.offset == (11 + words) % (1 << 128)
+        back = (1 << 128) - words  # below 2^64 words this is the rollback's (~w + 1, ~0)
+        lo, hi = back & ((1 << 64) - 1), back >> 64
+        lib = g.load()
+        assert lib.grng_engine_skip_ahead(e.handle, lo, hi) == 0
+        assert e.full_state == before
+
+
+def test_host_wrappers_refuse_n_beyond_the_tensor(g):
+    """n larger than the host tensor is refused before any copy is made."""
+    import torch
+
+    d = g.Distribution.uniform(0.0, 1.0, g.F32)
+    e = g.Engine(0, 1, 0)
+    host = torch.empty(4, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        g.generate_host(d, e, host, work=host, n=5)
+    with pytest.raises(ValueError):
+        g.generate_host_static(d, e, host, n=5)
+    with pytest.raises(ValueError):
+        g.generate_host_static(d, e, host, n=-1)
+    assert e.offset == 0

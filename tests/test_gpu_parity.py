@@ -309,3 +309,51 @@ def test_fill_equals_transform_of_its_words(g, engine_kind, var, n, offset, ptr_
     ref = out.cpu().numpy()
     bad = np.nonzero(_as_uint_view(got) != _as_uint_view(ref))[0]
     assert bad.size == 0, f"{var[0]}: {bad.size} differ, first at {bad[:5]}"
+
+
+def _fill_check(g, e, engine_kind, var, n, ref_fn, what):
+    _, kind, dtype, p0, p1 = var
+    out = torch.empty(n, dtype=_torch_dtype(dtype), device="cuda")
+    g.generate(g.Distribution(kind, dtype, p0, p1), e, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    ref = ref_fn(kind, dtype, p0, p1, n)
+    assert_parity(kind, dtype, got.view(np.uint32) if dtype == 0 else got, ref, what)
+
+
+@pytest.mark.parametrize("engine_kind", ENGINES)
+@pytest.mark.parametrize("seeded_by", ["seed", "words"])
+def test_copied_and_restored_engines_continue_the_sequence(g, engine_kind, seeded_by):
+    """Copy-constructed engines (oneMKL engines are copy-constructible, Sec. 4.1)
+    and engines restored from grng_engine_get_state generate, on the GPU, the
+    oracle's outputs from the offset the original had reached; the original
+    and its copy are independent afterwards."""
+    words = [0x9E3779B9, 17, 0xFFFFFFF0, 5, 6, 0x12345678]
+    var_a, var_b = VARIANTS[7], VARIANTS[4]  # gaussian F32, then uniform F64
+    if seeded_by == "seed":
+        e = g.Engine(engine_kind, 2021, 5)
+
+        def ref_at(off):
+            return lambda k, dt, p0, p1, n: oracle.generate(engine_kind, 2021, off, k, dt, p0, p1,
+                                                            n)
+    else:
+        e = g.Engine.from_words(engine_kind, words, offset=5)
+
+        def ref_at(off):
+            return lambda k, dt, p0, p1, n: oracle.generate_words(engine_kind, words, off, k, dt,
+                                                                  p0, p1, n)
+    # move the original mid-stream at an odd word phase
+    _fill_check(g, e, engine_kind, var_a, 1001, ref_at(5), "original")
+    off = e.offset
+    assert off == 5 + 1002
+    c = e.copy()
+    r = g.Engine.restore(e.full_state)
+    assert c.full_state == e.full_state == r.full_state
+    n = 65537
+    for eng, name in ((c, "copy"), (r, "restored"), (e, "original")):
+        _fill_check(g, eng, engine_kind, var_b, n, ref_at(off), name)
+    # each advanced by its own call only
+    for eng in (c, r, e):
+        assert eng.offset == off + 2 * n
+    _fill_check(g, c, engine_kind, var_a, 777, ref_at(off + 2 * n), "copy continues")
+    assert e.offset == off + 2 * n

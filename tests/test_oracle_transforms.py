@@ -2,7 +2,7 @@
 
 * Word -> uniform conversions are exact by definition: every one of the 2^24
   FP32 values and random FP64 values are compared with exact rational values.
-* The range transform of Sec. 3.3 (Listing 2) is checked for its half-open
+* The range transform of Sec. 4.3 (Listing 2) is checked for its half-open
   interval, its monotonicity, the cases where it is exact by arithmetic
   ([0,1), [-1,1), a + 0), a case where rounding reaches b and the clamp must
   fire, and its error bound against exact rational arithmetic.

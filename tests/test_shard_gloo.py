@@ -16,6 +16,14 @@ from paper_2109_01329_gb300 import shard
 CASES = [(0, 1, 1, 0.0, 1.0), (1, 2, 1, 0.0, 1.0), (0, 2, 2, 0.0, 1.0), (1, 0, 0, 0.0, 0.0)]
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    # shard.py takes word offsets from grng_words_for, so the library must exist
+    from paper_2109_01329_gb300 import build
+
+    build.build()
+
+
 def _worker(rank, world, port, n, q):
     import oracle
 

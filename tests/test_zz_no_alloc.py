@@ -21,7 +21,8 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-STAGE_BYTES = 64 << 20  # GRNG_STATIC_STAGE_BYTES
+# GRNG_STATIC_STAGE_BYTES, read from include/grng.h by the binding
+from paper_2109_01329_gb300._binding import STATIC_STAGE_BYTES as STAGE_BYTES  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -86,3 +87,20 @@ def test_size_limit_refused_engine_unchanged(g):
     host = torch.empty(STAGE_BYTES // 4, dtype=torch.float32)
     assert _static_call(g, g.Distribution(1, 1, 0.0, 1.0), e, host) == 0
     assert e.offset == STAGE_BYTES // 4
+
+
+def test_python_wrapper_two_calls(g):
+    """The binding's generate_host_static: two calls continue one sequence and
+    equal grng_generate; an n beyond the host tensor is refused before any
+    copy could write past it."""
+    d = g.Distribution.uniform(0.0, 1.0, g.F32)
+    e_static, e_ref = g.Engine(1, 99, 3), g.Engine(1, 99, 3)
+    for _ in range(2):
+        host = torch.empty(10_001, dtype=torch.float32)
+        g.generate_host_static(d, e_static, host)
+        dev = torch.empty(10_001, dtype=torch.float32, device="cuda")
+        g.generate(d, e_ref, dev)
+        assert np.array_equal(host.numpy().view(np.uint32), dev.cpu().numpy().view(np.uint32))
+    with pytest.raises(ValueError):
+        g.generate_host_static(d, e_static, torch.empty(4, dtype=torch.float32), n=5)
+    assert e_static.offset == e_ref.offset
