@@ -208,12 +208,45 @@ def oracle_rate(seconds_per_case: float, cores: int, n_cap: int):
 BM64_PRODUCTS_PER_PAIR = 42
 
 # DRAM bytes (read + write) per launch at n = 10^9 from ncu captures of the
-# current kernels: one launch of 2.68e8 samples scaled by 1e9 / 2.68e8
-# (profiles/gaussian_f64_2.68e8_full.md); replaced when a kernel changes.
+# current kernels: one launch of 2.68e8 samples scaled by 1e9 / 2.68e8;
+# a kernel whose code changed after its capture is left out (no number
+# rather than a stale one).
 NCU_TRAFFIC_PER_1E9 = {
     "mrg32k3a/gaussian_f64": (2.083029e9 + 0.160e6) / 0.268,
     "philox4x32_10/gaussian_f64": (2.083297e9 + 1.154e6) / 0.268,
 }
+
+# The method's own 32x32 -> 64-bit products per sample, independent of how
+# the kernels implement the arithmetic around them: two multiplier products
+# per Philox4x32-10 round, ten rounds per 4-word block (5 per word); two
+# multiplier products per MRG32k3a component step (4 per word; the modular
+# reductions are counted only in the implementation figures above).
+METHOD_PRODUCTS_PER_WORD = {"philox4x32_10": 5, "mrg32k3a": 4}
+WORDS_PER_SAMPLE = {"bits_u32": 1, "uniform_f32": 1, "uniform_f64": 2, "gaussian_f32": 1,
+                    "gaussian_f64": 2, "lognormal_f32": 1}
+
+# Method-level transcendental operations, evaluated by CUDA's math library in
+# the op-rate probes (csrc/probes.cu); samples/s a fill could reach if those
+# operations were its only work.  FP64 ones are context: the library computes
+# them in integer fixed point, off the FP64 pipe.
+OP_KINDS = {"fp32_box_muller_pair": 0, "fp32_expf": 1, "fp32_normcdfinvf": 2,
+            "fp64_box_muller_pair": 3, "fp64_fma": 4, "fp32_fma": 5, "xu_lg2_approx": 6,
+            "fp64_normcdfinv": 7}
+
+
+def transcendental_ceiling(name: str, ops: dict):
+    """(samples/s, what) of the method's transcendental operations, or None."""
+    if name == "gaussian_f32":
+        return 2 * ops["fp32_box_muller_pair"], "CUDA logf + sincospif + sqrtf per pair"
+    if name == "lognormal_f32":
+        t = 0.5 / ops["fp32_box_muller_pair"] + 1.0 / ops["fp32_expf"]
+        return 1.0 / t, "CUDA logf + sincospif + sqrtf per pair, expf per sample"
+    if name == "icdf_gaussian_f32":
+        return ops["fp32_normcdfinvf"], "CUDA normcdfinvf per sample"
+    if name == "icdf_lognormal_f32":
+        return 1.0 / (1.0 / ops["fp32_normcdfinvf"] + 1.0 / ops["fp32_expf"]), \
+            "CUDA normcdfinvf + expf per sample"
+    return None
 PRODUCTS_PER_SAMPLE = {
     "philox4x32_10/bits_u32": 5, "philox4x32_10/uniform_f32": 5,
     "philox4x32_10/uniform_f64": 10, "philox4x32_10/gaussian_f32": 5,
@@ -226,9 +259,18 @@ PRODUCTS_PER_SAMPLE = {
 
 
 def probe_ceilings(buf_ptr: int, nbytes: int, sink_ptr: int):
-    """Write-only bandwidth and the 32x32->64 product rate on this GPU."""
+    """Write-only bandwidth, the 32x32->64 product rate and the method-level
+    operation rates (OP_KINDS) on this GPU."""
     path = os.path.join(ROOT, "paper_2109_01329_gb300", "libgrng_probes.so")
     lib = ctypes.CDLL(path)
+    lib.grng_probe_op_rate.argtypes = [ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double)]
+    ops = {}
+    for nm, k in OP_KINDS.items():
+        r = ctypes.c_double()
+        if lib.grng_probe_op_rate(ctypes.c_void_p(sink_ptr), k, ctypes.byref(r)) != 0:
+            raise RuntimeError(f"op-rate probe {nm} failed")
+        ops[nm] = r.value
     lib.grng_probe_write_gbs.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_double)]
     lib.grng_probe_mulwide_rate.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
@@ -237,7 +279,7 @@ def probe_ceilings(buf_ptr: int, nbytes: int, sink_ptr: int):
         raise RuntimeError("write probe failed")
     if lib.grng_probe_mulwide_rate(ctypes.c_void_p(sink_ptr), ctypes.byref(m)) != 0:
         raise RuntimeError("multiply probe failed")
-    return w.value, m.value
+    return w.value, m.value, ops
 
 
 def aggregate_rate(rates: dict, n: int) -> float:
@@ -258,6 +300,66 @@ EXTRA_DISTS = [
     ("icdf_gaussian_f64", 4, 2, 0.0, 1.0), ("lognormal_f64", 3, 2, 0.0, 1.0),
     ("gaussian_f64_m3_s0.25", 2, 2, -3.0, 0.25), ("uniform_f32_2_5", 1, 1, 2.0, 5.0),
 ]
+
+
+def run_config1(grng, torch, dev, stream, reps=50):
+    """2^20 FP32 uniforms on [0, 1) from Philox4x32-10, seed 0x12345678, offset 0
+    (the bit-exact small case): device time per launch (CUDA events, median of
+    reps) and host time per call (launch overhead included)."""
+    n = 1 << 20
+    out = torch.empty(n, dtype=torch.float32, device=dev)
+    d = grng.Distribution.uniform(0.0, 1.0, grng.F32)
+    e = grng.Engine(0, 0x12345678, 0)
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            grng.generate(d, e, out, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            grng.generate(d, e, out, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        host = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            grng.generate(d, e, out, stream=stream)
+            host.append(time.perf_counter() - t0)
+        torch.cuda.synchronize()
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    return {"workload": "Philox4x32-10 seed 0x12345678 offset 0: 2^20 FP32 uniforms [0,1)",
+            "device_us": round(ms * 1e3, 2), "gsamples_s": round(n / ms / 1e6, 2),
+            "write_gbs": round(4 * n / ms / 1e6, 1),
+            "host_call_us": round(statistics.median(host) * 1e6, 2), "reps": reps,
+            "note": "4 MB: launch and ramp-up bound, far below the HBM roofline"}
+
+
+def run_config3(grng, torch, dev, stream, hbm_peak, reps=3):
+    """16384 substreams x 65536 FP64 gaussians (0, 1) in one launch per engine:
+    MRG32k3a substreams 2^76 words apart, Philox4x32-10 substreams 2^40 words
+    apart, seed 2021 (2^30 doubles = 8.6 GB per launch)."""
+    ns, per = 16384, 65536
+    out = torch.empty(ns * per, dtype=torch.float64, device=dev)
+    d = grng.Distribution.gaussian(0.0, 1.0, grng.F64)
+    res = {"workload": "16384 substreams x 65536 FP64 gaussians (0,1), seed 2021, one launch "
+                       "per engine (MRG32k3a stride 2^76, Philox4x32-10 stride 2^40)"}
+    for ek, en, stride in ((1, "mrg32k3a", 1 << 76), (0, "philox4x32_10", 1 << 40)):
+        e = grng.Engine(ek, W.SWEEP_SEED, 0)
+        with torch.cuda.stream(stream):
+            grng.generate_substreams(d, e, out, per, ns, stride, stream=stream)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(reps)]
+            for a, b in ev:
+                a.record(stream)
+                grng.generate_substreams(d, e, out, per, ns, stride, stream=stream)
+                b.record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        gbs = 8 * ns * per / ms / 1e6
+        res[en] = {"ms": round(ms, 3), "gsamples_s": round(ns * per / ms / 1e6, 2),
+                   "write_gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4)}
+    del out
+    return res
 
 
 def run_extra(grng, torch, dev, n, buf, stream, reps, hbm_peak):
@@ -364,7 +466,7 @@ def run_batched(grng, torch, dev, reps):
             e1.synchronize()
             loop_ms.append(e0.elapsed_time(e1))
         b = grng.Batch(reqs, ipt=8, stream=stream)
-        ctas, tune_ms = b.autotune(stream=stream)
+        ipt, ctas, tune_ms = b.autotune(stream=stream)
         b.launch(stream=stream)
         stream.synchronize()
         graph = torch.cuda.CUDAGraph()
@@ -393,11 +495,12 @@ def run_batched(grng, torch, dev, reps):
             "batched_gsamples_s": round(total / med_batch / 1e6, 2),
             "batched_write_gbs": round(out_bytes / med_batch / 1e6, 1),
             "per_request_gsamples_s": round(total / med_loop / 1e6, 2),
-            "autotune": {"ctas_per_sm": ctas, "ms": round(tune_ms, 4), "ipt": 8},
+            "autotune": {"ipt": ipt, "ctas_per_sm": ctas, "ms": round(tune_ms, 4),
+                         "searched": "ipt {1,2,4,8,16,32} x CTAs/SM {1,2,4,6,8,12,16}"},
             "reps": reps}
 
 
-def run_serving(grng, torch, dev, seconds, stress):
+def run_serving(grng, torch, dev, seconds, stress, hold):
     """FastCaloSim-shaped serving.  Poisson arrivals at 2000 events/s,
     hits ~ lognormal(mean 8000, sigma 0.8) clipped to [100, 200000]; each event
     = 3h FP32 uniforms + h FP32 gaussians from its own Philox engine (seed =
@@ -413,15 +516,22 @@ def run_serving(grng, torch, dev, seconds, stress):
                        "3 stream slots",
            "events": len(reqs), "samples": int(4 * hits.sum())}
     srv = grng.Server(4 << 30, num_streams=3, auto_release=True, device=dev)
-    # the burst (every event at once) lasts a few tens of milliseconds, so it is
-    # replayed five times and the median run is reported
-    for name, scale, runs in (("real_time", 1.0, 1), (f"stress_{stress:g}x", 1.0 / stress, 1),
-                              ("burst", 1e-9, 5)):
+    # real time; then compressed `stress` times with every output held for
+    # `hold` seconds after completion (a consumer that keeps each event's
+    # numbers that long), so that the 4 GB budget binds and admission waits;
+    # the burst (every event at once) lasts a few tens of milliseconds, so it
+    # is replayed five times and the median run is reported
+    for name, scale, runs, hold_s in (("real_time", 1.0, 1, 0.0),
+                                      (f"stress_{stress:g}x_hold_{hold:g}s", 1.0 / stress, 1, hold),
+                                      ("burst", 1e-9, 5, 0.0)):
         results = []
+        srv.set_release_delay(hold_s)
         for _ in range(runs):
             srv.reset_stats()
             srv.replay(t, reqs, time_scale=scale)
             srv.drain(timeout_s=600)
+            if hold_s > 0:
+                time.sleep(hold_s + 0.2)  # the held outputs go back to the budget
             st = srv.stats()
             results.append({
                 "gsamples_s": round(st["samples"] / st["wall_s"] / 1e9, 3) if st["wall_s"]
@@ -433,6 +543,8 @@ def run_serving(grng, torch, dev, seconds, stress):
                 "batches": st["batches"],
                 "mean_batch_events": round(st["mean_batch_requests"], 2),
                 "peak_pool_gb": round(st["peak_pool_bytes"] / 1e9, 3),
+                "admit_wait_p50_us": round(st["admit_wait_p50_us"], 1),
+                "admit_wait_p99_us": round(st["admit_wait_p99_us"], 1),
                 "wall_s": round(st["wall_s"], 3)})
         results.sort(key=lambda r: r["gsamples_s"] or 0.0)
         out[name] = dict(results[len(results) // 2])
@@ -474,6 +586,18 @@ def sweep_config(n: int, world: int) -> dict:
             "l2": "every fill writes 4-8 GB, larger than the 129 MB L2"}
 
 
+def _long_double_note() -> str:
+    """How the oracle's long double arithmetic runs on this host."""
+    import platform
+
+    m = platform.machine()
+    if m in ("aarch64", "arm64"):
+        return ("the oracle evaluates Box-Muller and the inverse CDF in long double, which on "
+                "this aarch64 host is IEEE binary128 in software (so its gaussian and lognormal "
+                "cases run about 20x slower than its uniforms)")
+    return f"the oracle evaluates Box-Muller and the inverse CDF in long double ({m} host)"
+
+
 def run_reference(args):
     """The oracle as the reference arm: bounded samples of the sweep per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -506,7 +630,7 @@ def run_reference(args):
     value = samples / dt / 1e9
     sample_desc = (f"{chunk * cores} samples per (engine, distribution) case per step, "
                    f"{len(ENGINES) * len(W.SWEEP_DISTS)} cases, seed 2021, split over {cores} "
-                   "threads by word offset")
+                   "threads by word offset; " + _long_double_note())
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -572,6 +696,15 @@ def run_ours(args):
             if events is not None:
                 events[i][1].record(stream)
 
+    # launch geometry per fill from the library's autotuner (the outputs do not
+    # depend on it); the choice is reported per kernel
+    geometry = {}
+    for ek, en, (name, kind, dtype, p0, p1) in cases:
+        d = grng.Distribution(kind, dtype, p0, p1)
+        es = 8 if dtype == 2 else 4
+        if not args.no_tune:
+            grng.fill_autotune(ek, d, buf[: n * es].view(tdt[dtype]), n, stream=stream)
+        geometry[f"{en}/{name}"] = grng.fill_geometry(ek, d, n)
     for _ in range(max(args.warmup, 0)):
         one_step()
     torch.cuda.synchronize()
@@ -604,7 +737,7 @@ def run_ours(args):
 
     # ceilings measured live on this GPU (outside the timed region)
     sink = torch.zeros(16, dtype=torch.int32, device=dev)
-    write_gbs, mul_probe = probe_ceilings(buf.data_ptr(), buf.numel(), sink.data_ptr())
+    write_gbs, mul_probe, ops = probe_ceilings(buf.data_ptr(), buf.numel(), sink.data_ptr())
     # integer roofline peak from unit counts and the clock: per SM 4 sub-partitions
     # x 16 lanes of the FMA-heavy pipe, a 32x32->64 product taking two passes,
     # i.e. 32 products per clock per SM, at the median SM clock under load
@@ -616,30 +749,55 @@ def run_ours(args):
         key = f"{en}/{name}"
         ms = statistics.median(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
         es = 8 if dtype == 2 else 4
+        rate = n / (ms * 1e-3)
         gbs = n * es / (ms * 1e-3) / 1e9
         prods = PRODUCTS_PER_SAMPLE[key] * n
         tops = prods / (ms * 1e-3) / 1e12
-        # roofline = min(HBM bound, product-rate bound), in samples/s
-        hbm_cap = hbm_peak * 1e9 / es
-        int_cap = mul_rate / PRODUCTS_PER_SAMPLE[key]
-        bound = "hbm" if hbm_cap <= int_cap else "alu"
-        per_kernel[key] = {"ms": round(ms, 4), "gsamples_s": round(n / ms / 1e6, 2),
+        m_prods = METHOD_PRODUCTS_PER_WORD[en] * WORDS_PER_SAMPLE[name]
+        # ceilings in samples/s: the roofline of the target statement is the
+        # slower of output bytes at HBM bandwidth and integer operations at
+        # peak (the products as implemented); the method view counts only the
+        # method's own products; FP32 transcendental fills add the rate of
+        # their method operations in CUDA's math library
+        ceil = {"hbm_write": hbm_peak * 1e9 / es, "int_impl": mul_rate / PRODUCTS_PER_SAMPLE[key],
+                "int_method": mul_rate / m_prods}
+        tc = transcendental_ceiling(name, ops)
+        if tc is not None:
+            ceil["transcendental"] = tc[0]
+        impl_keys = [c for c in ceil if c != "int_method"]
+        meth_keys = [c for c in ceil if c != "int_impl"]
+        bound = min(impl_keys, key=ceil.get)
+        bound_m = min(meth_keys, key=ceil.get)
+        per_kernel[key] = {"ms": round(ms, 4), "gsamples_s": round(rate / 1e9, 2),
                            "write_gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4),
+                           "frac_write_probe": round(gbs / write_gbs, 4),
                            "products_per_launch": prods, "tproducts_s": round(tops, 3),
                            "frac_int": round(tops * 1e12 / mul_rate, 4),
-                           "bound": bound,
-                           "frac_roofline": round((n / (ms * 1e-3)) / min(hbm_cap, int_cap), 4)}
+                           "frac_int_method": round(rate * m_prods / mul_rate, 4),
+                           "ceilings_gsamples_s": {c: round(v / 1e9, 2) for c, v in ceil.items()},
+                           "bound": "hbm" if bound == "hbm_write" else "alu",
+                           "bound_ceiling": bound,
+                           "frac_roofline": round(rate / ceil[bound], 4),
+                           "bound_ceiling_method": bound_m,
+                           "frac_roofline_method": round(rate / ceil[bound_m], 4)}
+        if tc is not None:
+            per_kernel[key]["transcendental_ops"] = tc[1]
+        per_kernel[key]["geometry"] = geometry[key]
+        if name == "gaussian_f64":
+            # context: the method's FP64 operations in CUDA's FP64 math library
+            per_kernel[key]["vs_fp64_libm_rate"] = round(
+                rate / (2 * ops["fp64_box_muller_pair"]), 2)
     dom_name = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     dom = per_kernel[dom_name]
     traffic = args.traffic
     if traffic is None and dom_name in NCU_TRAFFIC_PER_1E9:
         traffic = round(NCU_TRAFFIC_PER_1E9[dom_name] * n / 1e9)
-    if dom["bound"] == "hbm":
+    if dom["bound_ceiling"] == "hbm_write":
         roofline = {"kernel": dom_name, "bound": "hbm", "achieved": dom["write_gbs"],
                     "peak": hbm_peak, "unit": "GB/s", "frac": dom["frac_hbm"],
                     "traffic": traffic, "peak_source": f"{peak_src} hbm_gbs (copy)",
                     "bytes_per_launch": n * (8 if "f64" in dom_name else 4)}
-    else:
+    elif dom["bound_ceiling"] == "int_impl":
         roofline = {"kernel": dom_name, "bound": "alu", "achieved": dom["tproducts_s"],
                     "peak": round(mul_rate / 1e12, 3), "unit": "T products/s (32x32->64)",
                     "frac": dom["frac_int"], "traffic": traffic,
@@ -648,7 +806,24 @@ def run_ours(args):
                                    f"reaches {mul_probe / 1e12:.2f} T/s)",
                     "products_per_launch": dom["products_per_launch"],
                     "bytes_per_launch": n * (8 if "f64" in dom_name else 4)}
+    else:
+        roofline = {"kernel": dom_name, "bound": "alu", "achieved": dom["gsamples_s"],
+                    "peak": dom["ceilings_gsamples_s"]["transcendental"], "unit": "Gsamples/s",
+                    "frac": dom["frac_roofline"], "traffic": traffic,
+                    "peak_source": "live probe: " + dom["transcendental_ops"],
+                    "bytes_per_launch": n * (8 if "f64" in dom_name else 4)}
+    roofline["method_view"] = {"bound_ceiling": dom["bound_ceiling_method"],
+                               "frac": dom["frac_roofline_method"],
+                               "ceilings_gsamples_s": dom["ceilings_gsamples_s"]}
     target = per_kernel.get("philox4x32_10/uniform_f32", dom)
+    # the target statement's headline: Philox FP32 uniform fill at >= 0.80 of
+    # its roofline (HBM write bound), against the copy peak and the live
+    # write-only probe
+    roofline["target_philox_uniform_f32"] = {
+        "write_gbs": target["write_gbs"], "frac": target["frac_roofline"],
+        "frac_hbm_copy_peak": target["frac_hbm"],
+        "frac_write_only_probe": target["frac_write_probe"],
+        "write_only_probe_gbs": round(write_gbs, 1), "meets_0_80": target["frac_roofline"] >= 0.80}
 
     # cuRAND on the same fills (generate calls only; generator created outside)
     curand = None
@@ -745,13 +920,19 @@ def run_ours(args):
     if rank == 0 and not args.skip_extra:
         extra = run_extra(grng, torch, dev, n, buf, stream, 3, hbm_peak)
 
+    config1 = config3 = None
+    if rank == 0 and not args.skip_configs:
+        config1 = run_config1(grng, torch, dev, stream)
+        config3 = run_config3(grng, torch, dev, stream, hbm_peak)
+
     batched = None
     if rank == 0 and not args.skip_batched:
         batched = run_batched(grng, torch, dev, args.batch_reps)
 
     serving = None
     if rank == 0 and args.serve_seconds > 0:
-        serving = run_serving(grng, torch, dev, args.serve_seconds, args.serve_stress)
+        serving = run_serving(grng, torch, dev, args.serve_seconds, args.serve_stress,
+                              args.serve_hold)
 
     cpu = None
     if rank == 0 and not args.skip_cpu:
@@ -761,7 +942,7 @@ def run_ours(args):
                "kind": "oracle",
                "sample": f"about {args.cpu_seconds:g} s per (engine, distribution) case, "
                          f"chunks of 16384 samples over {cores} threads by word offset; rate "
-                         "scaled to the sweep step (n per case)",
+                         "scaled to the sweep step (n per case); " + _long_double_note(),
                "per_case": {k: {"gsamples_s": round(rates[k] / 1e9, 6), **detail[k]}
                             for k in rates}}
 
@@ -776,8 +957,10 @@ def run_ours(args):
                                           "frac_roofline": target["frac_roofline"],
                                           "gsamples_s": target["gsamples_s"]},
             "ceilings": {"hbm_copy_gbs": hbm_peak, "write_only_gbs": round(write_gbs, 1),
-                         "products_per_s": mul_rate, "products_per_s_probe": mul_probe},
+                         "products_per_s": mul_rate, "products_per_s_probe": mul_probe,
+                         "op_rates_per_s": {k: round(v, 1) for k, v in ops.items()}},
             "per_kernel": per_kernel, "curand": curand, "tts": tts, "other_fills": extra,
+            "config1_2pow20_uniform": config1, "config3_substreams": config3,
             "batched": batched, "serving": serving,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": args.steps * len(cases)}
@@ -807,12 +990,18 @@ def main():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-tts", action="store_true",
                     help="skip the time-to-solution calls (create + seed + fill + sync)")
+    ap.add_argument("--skip-configs", action="store_true",
+                    help="skip the timed small case (2^20 uniforms) and the substream launches")
     ap.add_argument("--skip-extra", action="store_true",
                     help="skip the fills outside the sweep (inverse CDF, FP64 lognormal, ...)")
     ap.add_argument("--batch-reps", type=int, default=20)
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="seconds of the arrival trace to replay in real time (0: skip)")
     ap.add_argument("--serve-stress", type=float, default=20.0)
+    ap.add_argument("--serve-hold", type=float, default=1.0,
+                    help="seconds each output is held after completion in the stress replay")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the built-in launch geometry instead of autotuning each fill")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()

@@ -250,6 +250,44 @@ GRNG_API grng_status grng_generate_host(const grng_distribution* dist, grng_engi
                                void* host_ptr, void* dev_work, size_t work_bytes,
                                grng_stream_t stream);
 
+/* ---------------------------------------------------------- fill geometry
+ * Launch geometry of grng_generate / grng_generate_substreams, one integer
+ * per (engine kind, distribution variant, size bucket = bit length of the
+ * element count): Philox4x32-10, the cap on resident CTAs per SM (the kernels
+ * loop with a grid stride); MRG32k3a, the threads per SM of the chunk plan in
+ * units of 256 (sets the chunk length); 0 = the built-in choice.  Tuning is
+ * what the paper expects of kernels written for the hardware (Sec. 8; Sec. 7
+ * shows the launch configuration mattering).  Outputs never depend on the
+ * geometry.  The table starts from the file named by the environment
+ * variable GRNG_TUNE_CACHE, if it exists, when first read.  The table is
+ * process-wide; the calls below may race with fills on other threads only
+ * in which geometry those fills use.
+ */
+
+/* Times a fill of n outputs of `dist` into dev_buf (caller-owned device
+ * memory of n elements, aligned to the element size) at each candidate
+ * geometry (Philox: 0, 1, 2, 3, 4, 5, 6, 8; MRG32k3a: 0, 1, 2, 4, 6, 12, 16),
+ * with a private engine (no caller engine moves), and keeps the fastest for
+ * n's bucket; *best_geometry and *best_ms (either may be NULL) receive it.
+ * Synchronises `stream`.  Errors: INVALID_ARG (bad kind, dist, n < 1, NULL
+ * dev_buf), CUDA. */
+GRNG_API grng_status grng_fill_autotune(int32_t engine_kind, const grng_distribution* dist,
+                                        int64_t n, void* dev_buf, grng_stream_t stream,
+                                        int32_t* best_geometry, float* best_ms);
+
+/* Sets / reads the geometry of n's bucket (0..64; 0 = built-in). */
+GRNG_API grng_status grng_fill_set_geometry(int32_t engine_kind, const grng_distribution* dist,
+                                            int64_t n, int32_t geometry);
+GRNG_API grng_status grng_fill_get_geometry(int32_t engine_kind, const grng_distribution* dist,
+                                            int64_t n, int32_t* geometry);
+
+/* Writes the table's non-default entries to `path` ("grng-tune 1", then one
+ * "engine variant bucket geometry" line per entry), reads such a file into
+ * the table, or resets every entry to 0. */
+GRNG_API grng_status grng_tune_save(const char* path);
+GRNG_API grng_status grng_tune_load(const char* path);
+GRNG_API grng_status grng_tune_reset(void);
+
 /* ------------------------------------------------------------------ batches
  * Many independent requests in one persistent launch: the event batching the
  * paper names as future work for FastCaloSim (Sec. 7), where per-call
@@ -289,14 +327,25 @@ GRNG_API grng_status grng_batch_create(grng_batch_t* out, const grng_request* re
  * synchronisation, no allocation; may be captured into a CUDA graph. */
 GRNG_API grng_status grng_batch_launch(grng_batch_t batch, grng_stream_t stream);
 
-/* Times the fill at several CTAs-per-SM settings (without advancing the
- * offsets: the outputs are rewritten identically) and keeps the fastest;
- * *best_ctas and *best_ms (either may be NULL) receive the choice. */
+/* The autotuner of the batched fill (Sec. 8 names tuning as the cost of
+ * portable native kernels; Sec. 7 shows small batches dominated by per-call
+ * overheads).  Times the fill over the launch geometries ipt (16-byte groups
+ * per thread per tile: 1, 2, 4, 8, 16, 32) x CTAs per SM (1, 2, 4, 6, 8, 12,
+ * 16), without advancing the offsets (the outputs are rewritten
+ * identically), and keeps the fastest.  Only the ipt values whose tile map
+ * fits the workspace given to grng_batch_create are tried: a workspace of
+ * grng_batch_workspace_bytes(..., ipt = 1, ...) admits every one.  The
+ * output never depends on the geometry.  *best_ipt, *best_ctas and *best_ms
+ * (each may be NULL) receive the choice.  Synchronises `stream`.  A CUDA
+ * graph captured before a change of ipt must be captured again. */
 GRNG_API grng_status grng_batch_autotune(grng_batch_t batch, grng_stream_t stream,
-                                         int32_t* best_ctas, float* best_ms);
+                                         int32_t* best_ipt, int32_t* best_ctas, float* best_ms);
 
-/* Sets the CTAs-per-SM of the fill (1..32), e.g. from a saved tuning. */
-GRNG_API grng_status grng_batch_set_config(grng_batch_t batch, int32_t ctas_per_sm);
+/* Sets the fill's geometry (ipt 1..64, CTAs per SM 1..32), e.g. from a
+ * saved tuning; re-plans the tile map in the workspace when ipt changes
+ * (synchronising `stream`).  INVALID_ARG if that map does not fit. */
+GRNG_API grng_status grng_batch_set_config(grng_batch_t batch, int32_t ipt, int32_t ctas_per_sm,
+                                           grng_stream_t stream);
 
 /* Moves each engine of the batch to its device-resident offset (after the
  * launches so far).  Synchronises `stream`. */
@@ -339,6 +388,7 @@ typedef struct grng_serve_stats {
   double latency_p50_us, latency_p90_us, latency_p99_us, latency_max_us, latency_mean_us;
   double peak_pool_bytes;    /* high-water mark of admitted output bytes */
   double mean_batch_requests;
+  double admit_wait_p50_us, admit_wait_p99_us, admit_wait_max_us; /* arrival to admission */
 } grng_serve_stats;
 
 typedef struct grng_server* grng_server_t;
@@ -367,10 +417,18 @@ GRNG_API grng_status grng_server_release(grng_server_t server, uint64_t ticket);
 /* Waits up to timeout_us until nothing is queued or running. */
 GRNG_API grng_status grng_server_drain(grng_server_t server, int64_t timeout_us);
 
-/* Counters and arrival-to-completion latency percentiles since creation or
- * the last reset. */
+/* Counters, arrival-to-completion latency and arrival-to-admission wait
+ * percentiles since creation or the last reset. */
 GRNG_API grng_status grng_server_stats(grng_server_t server, grng_serve_stats* out);
 GRNG_API grng_status grng_server_reset_stats(grng_server_t server);
+
+/* With GRNG_SERVE_AUTO_RELEASE, keeps each completed output in the budget
+ * for delay_us microseconds after its completion before freeing it (a
+ * consumer that holds every output that long; 0, the default, frees at
+ * completion).  When outputs arrive faster than they are let go, the budget
+ * binds and admission waits.  A reading of Sec. 5.2's event-by-event demand,
+ * not in the paper.  Errors: INVALID_ARG (NULL server, delay_us < 0). */
+GRNG_API grng_status grng_server_set_release_delay(grng_server_t server, int64_t delay_us);
 
 /* Submits reqs[i] at arrival_s[i] * time_scale seconds after the call (a
  * trace replay driven from the calling thread); returns after the last

@@ -22,6 +22,12 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "grng_oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# Test hook: tests/test_oracle_planted.py builds deliberately broken copies of
+# the source (one planted mistake each) and runs the pins against them; the
+# library of such a copy is built next to it.
+if os.environ.get("GRNG_ORACLE_SRC"):
+    _SRC = os.path.abspath(os.environ["GRNG_ORACLE_SRC"])
+    _LIB = os.path.join(os.path.dirname(_SRC), "liboracle.so")
 
 ENGINE_PHILOX = 0
 ENGINE_MRG = 1

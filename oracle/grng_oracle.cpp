@@ -45,10 +45,12 @@
 // Philox4x32-10; MRG32k3a has full-period transition matrices (orders checked
 // against sympy's primitivity test), jumps equal stepping, powers compose;
 // conversions equal exact rationals; Box-Muller matches closed forms and the
-// normal / lognormal laws.  One step has no pin beyond its published
-// definition: the sign of the MRG32k3a output combination z = x1 - x2 (both
-// signs give statistically identical streams and no known-answer vectors are
-// at hand): parity unpinned for that step.
+// normal / lognormal laws.  The sign of the MRG32k3a output combination
+// z = x1 - x2 (both signs give statistically identical streams, so no CPU
+// pin sees it) is pinned on the GPU against cuRAND's independent MRG32k3a,
+// driven as a black box (tests/test_gpu_curand_pin.py), which also checks the
+// Philox blocks a second time.  tests/test_oracle_planted.py plants 28
+// plausible single mistakes in copies of this file; each fails a CPU pin.
 //
 // Built with -O2 -ffp-contract=off so that no multiply-add is contracted.
 

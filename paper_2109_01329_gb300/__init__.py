@@ -10,10 +10,12 @@ binding.
 from ._binding import (BITS, GAUSSIAN_ICDF, LOGNORMAL_ICDF, Batch, Server, serve_request, F32, F64, GAUSSIAN, LOGNORMAL, MRG32K3A, PHILOX4X32X10, U32,
                        UNIFORM, Distribution, Engine, GrngError, generate, generate_host,
                        generate_host_static,
-                       generate_ptr, generate_substreams, load, transform_words, words_for)
+                       generate_ptr, generate_substreams, load, transform_words, words_for,
+                       fill_autotune, fill_geometry, tune_save, tune_load, tune_reset)
 from ._binding import LIB_PATH, EXPORTED
 
 __all__ = ["BITS", "GAUSSIAN_ICDF", "LOGNORMAL_ICDF", "Batch", "Server", "serve_request", "F32", "F64", "GAUSSIAN", "LOGNORMAL", "MRG32K3A", "PHILOX4X32X10", "U32",
            "UNIFORM", "Distribution", "Engine", "GrngError", "generate", "generate_host",
            "generate_host_static",
-           "generate_ptr", "generate_substreams", "load", "transform_words", "words_for", "LIB_PATH", "EXPORTED"]
+           "generate_ptr", "generate_substreams", "load", "transform_words", "words_for", "LIB_PATH", "EXPORTED",
+           "fill_autotune", "fill_geometry", "tune_save", "tune_load", "tune_reset"]

@@ -35,7 +35,9 @@ EXPORTED = ["grng_status_string", "grng_last_error", "grng_engine_create",
             "grng_batch_commit", "grng_batch_destroy", "grng_server_create",
             "grng_server_submit", "grng_server_wait", "grng_server_release", "grng_server_drain",
             "grng_server_stats", "grng_server_reset_stats", "grng_server_replay",
-            "grng_server_destroy"]
+            "grng_server_destroy", "grng_server_set_release_delay", "grng_fill_autotune",
+            "grng_fill_set_geometry", "grng_fill_get_geometry", "grng_tune_save",
+            "grng_tune_load", "grng_tune_reset"]
 
 
 class GrngError(RuntimeError):
@@ -77,7 +79,8 @@ class _ServeStats(ctypes.Structure):
                 ("latency_p50_us", ctypes.c_double), ("latency_p90_us", ctypes.c_double),
                 ("latency_p99_us", ctypes.c_double), ("latency_max_us", ctypes.c_double),
                 ("latency_mean_us", ctypes.c_double), ("peak_pool_bytes", ctypes.c_double),
-                ("mean_batch_requests", ctypes.c_double)]
+                ("mean_batch_requests", ctypes.c_double), ("admit_wait_p50_us", ctypes.c_double),
+                ("admit_wait_p99_us", ctypes.c_double), ("admit_wait_max_us", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -127,8 +130,9 @@ def load() -> ctypes.CDLL:
                                         ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, vp]
         L.grng_batch_launch.argtypes = [vp, vp]
         L.grng_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_float)]
-        L.grng_batch_set_config.argtypes = [vp, ctypes.c_int32]
+        L.grng_batch_set_config.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp]
         L.grng_batch_commit.argtypes = [vp, vp]
         L.grng_batch_destroy.argtypes = [vp]
         L.grng_server_create.argtypes = [ctypes.POINTER(vp), vp, ctypes.c_size_t, ctypes.c_int32,
@@ -145,6 +149,17 @@ def load() -> ctypes.CDLL:
                                          ctypes.POINTER(_ServeRequest), ctypes.c_int64,
                                          ctypes.c_double]
         L.grng_server_destroy.argtypes = [vp]
+        L.grng_server_set_release_delay.argtypes = [vp, ctypes.c_int64]
+        L.grng_fill_autotune.argtypes = [ctypes.c_int32, ctypes.POINTER(_Dist), ctypes.c_int64, vp,
+                                         vp, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_float)]
+        L.grng_fill_set_geometry.argtypes = [ctypes.c_int32, ctypes.POINTER(_Dist),
+                                             ctypes.c_int64, ctypes.c_int32]
+        L.grng_fill_get_geometry.argtypes = [ctypes.c_int32, ctypes.POINTER(_Dist),
+                                             ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]
+        L.grng_tune_save.argtypes = [ctypes.c_char_p]
+        L.grng_tune_load.argtypes = [ctypes.c_char_p]
+        L.grng_tune_reset.argtypes = []
         for name in EXPORTED[2:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -431,6 +446,53 @@ def generate_host_static(dist: Distribution, engine: Engine, host_out, n: int | 
     return host_out
 
 
+def fill_autotune(engine_kind: int, dist: Distribution, buf, n: int | None = None,
+                  stream=None):
+    """grng_fill_autotune: times the candidate launch geometries of a fill of n
+    outputs into the CUDA tensor buf and keeps the fastest for n's size
+    bucket; returns (geometry, ms)."""
+    import torch
+
+    if not buf.is_cuda or not _torch_dtype_ok(buf, dist.dtype):
+        raise ValueError("buf must be a CUDA tensor of the distribution's dtype")
+    n = buf.numel() if n is None else n
+    if n < 1 or n > buf.numel():
+        raise ValueError("n outside [1, buf.numel()]")
+    d = dist._c()
+    geo, ms = ctypes.c_int32(), ctypes.c_float()
+    with torch.cuda.device(buf.device):
+        _check(load().grng_fill_autotune(engine_kind, ctypes.byref(d), n,
+                                         ctypes.c_void_p(buf.data_ptr()),
+                                         ctypes.c_void_p(_stream_ptr(buf.device, stream)),
+                                         ctypes.byref(geo), ctypes.byref(ms)),
+               "grng_fill_autotune")
+    return geo.value, ms.value
+
+
+def fill_geometry(engine_kind: int, dist: Distribution, n: int, geometry: int | None = None) -> int:
+    """Reads (or, with geometry, sets) the launch geometry of n's size bucket."""
+    d = dist._c()
+    if geometry is not None:
+        _check(load().grng_fill_set_geometry(engine_kind, ctypes.byref(d), n, geometry),
+               "grng_fill_set_geometry")
+    g = ctypes.c_int32()
+    _check(load().grng_fill_get_geometry(engine_kind, ctypes.byref(d), n, ctypes.byref(g)),
+           "grng_fill_get_geometry")
+    return g.value
+
+
+def tune_save(path: str) -> None:
+    _check(load().grng_tune_save(os.fsencode(path)), "grng_tune_save")
+
+
+def tune_load(path: str) -> None:
+    _check(load().grng_tune_load(os.fsencode(path)), "grng_tune_load")
+
+
+def tune_reset() -> None:
+    _check(load().grng_tune_reset(), "grng_tune_reset")
+
+
 def transform_words(dist: Distribution, words, out, n: int | None = None, stream=None):
     """grng_transform_words: applies dist to the device words tensor (int32 / uint32)."""
     import torch
@@ -456,12 +518,13 @@ class Batch:
 
     requests: list of (engine, distribution, out_tensor[, n]).  The device
     workspace is allocated here as a torch tensor and kept alive with the
-    batch.  launch() enqueues the persistent fill and the device-side offset
-    advance (capturable in a CUDA graph); commit() moves the engines to the
-    device-resident offsets.
+    batch; with tunable=True it is sized for ipt = 1, so that autotune() may
+    try every geometry.  launch() enqueues the persistent fill and the
+    device-side offset advance (capturable in a CUDA graph); commit() moves
+    the engines to the device-resident offsets.
     """
 
-    def __init__(self, requests, ipt: int = 8, stream=None):
+    def __init__(self, requests, ipt: int = 8, stream=None, tunable: bool = True):
         import torch
 
         self._reqs = list(requests)
@@ -482,8 +545,8 @@ class Batch:
         self._arr = arr
         L = load()
         nbytes = ctypes.c_size_t()
-        _check(L.grng_batch_workspace_bytes(arr, len(arr), ipt, ctypes.byref(nbytes)),
-               "grng_batch_workspace_bytes")
+        _check(L.grng_batch_workspace_bytes(arr, len(arr), 1 if tunable else ipt,
+                                            ctypes.byref(nbytes)), "grng_batch_workspace_bytes")
         self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
         self._dev = dev
         self._h = ctypes.c_void_p()
@@ -501,17 +564,23 @@ class Batch:
                    "grng_batch_launch")
 
     def autotune(self, stream=None):
+        """(ipt, CTAs per SM, ms per fill) of the fastest geometry, now in use."""
         import torch
 
-        c, ms = ctypes.c_int32(), ctypes.c_float()
+        i, c, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
         with torch.cuda.device(self._dev):
             _check(load().grng_batch_autotune(self._h, ctypes.c_void_p(_stream_ptr(self._dev, stream)),
-                                              ctypes.byref(c), ctypes.byref(ms)),
+                                              ctypes.byref(i), ctypes.byref(c), ctypes.byref(ms)),
                    "grng_batch_autotune")
-        return c.value, ms.value
+        return i.value, c.value, ms.value
 
-    def set_config(self, ctas_per_sm: int):
-        _check(load().grng_batch_set_config(self._h, ctas_per_sm), "grng_batch_set_config")
+    def set_config(self, ipt: int, ctas_per_sm: int, stream=None):
+        import torch
+
+        with torch.cuda.device(self._dev):
+            _check(load().grng_batch_set_config(self._h, ipt, ctas_per_sm,
+                                                ctypes.c_void_p(_stream_ptr(self._dev, stream))),
+                   "grng_batch_set_config")
 
     def commit(self, stream=None):
         import torch
@@ -598,6 +667,12 @@ class Server:
 
     def reset_stats(self) -> None:
         _check(load().grng_server_reset_stats(self._h), "grng_server_reset_stats")
+
+    def set_release_delay(self, seconds: float) -> None:
+        """With auto_release: each output stays in the budget this long after
+        completion (a consumer holding it), so the budget can bind."""
+        _check(load().grng_server_set_release_delay(self._h, int(seconds * 1e6)),
+               "grng_server_set_release_delay")
 
     def replay(self, arrivals, requests, time_scale: float = 1.0) -> None:
         n = len(requests)

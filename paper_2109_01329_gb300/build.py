@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "libgrng.so")
 PROBES_PATH = os.path.join(HERE, "libgrng_probes.so")
 
 SOURCES = ["capi.cpp", "philox_kernels.cu", "mrg_kernels.cu", "static_stage.cu",
-           "transform_kernels.cu", "batch.cu", "serve.cpp"]
+           "transform_kernels.cu", "batch.cu", "serve.cpp", "tune.cpp"]
 HEADERS = ["device_common.cuh", "grng_internal.h", "mrg_tables.h", "bm64_fixed.cuh",
            "bm64_tables.h", "icdf64_fixed.cuh", "icdf64_tables.h", "icdf32_tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -305,7 +305,10 @@ struct grng_batch {
   int32_t sms;
   int32_t device;
   void* workspace;
+  size_t workspace_bytes;
   size_t reqs_off, offs_off, tiles_off;
+  std::vector<grng::BatchReq> host_reqs;  // the request records as uploaded
+  std::vector<int64_t> groups;            // per request
   int64_t groups_total;
   std::vector<grng_engine_t> engines;  // per request
   std::vector<int32_t> first_req_of_engine;  // per request: index of its engine's first request
@@ -489,6 +492,8 @@ grng_status grng_batch_create(grng_batch_t* out, const grng_request* reqs, int32
     t += nt;
     b->groups_total += groups[i];
   }
+  b->workspace_bytes = workspace_bytes;
+  b->groups = groups;
   char* ws = reinterpret_cast<char*>(dev_workspace);
   cudaError_t err =
       cudaMemcpyAsync(ws + b->reqs_off, h.data(), sizeof(BatchReq) * (size_t)count,
@@ -507,15 +512,78 @@ grng_status grng_batch_create(grng_batch_t* out, const grng_request* reqs, int32
     delete b;
     return GRNG_ERR_CUDA;
   }
+  b->host_reqs = std::move(h);
   *out = b;
   return GRNG_OK;
 }
 
-grng_status grng_batch_set_config(grng_batch_t b, int32_t ctas_per_sm) {
-  if (b == nullptr || ctas_per_sm < 1 || ctas_per_sm > 32) {
-    set_error("bad batch or ctas_per_sm");
+}  // extern "C"
+
+namespace {
+
+// Tiles of the batch at ipt groups per thread, and whether their map fits the
+// workspace given at creation.
+int64_t tiles_at(const grng_batch* b, int ipt) {
+  const int64_t tile_groups = (int64_t)kThreads * ipt;
+  int64_t t = 0;
+  for (int64_t g : b->groups) t += (g + tile_groups - 1) / tile_groups;
+  return t;
+}
+bool fits(const grng_batch* b, int ipt) {
+  const int64_t t = tiles_at(b, ipt);
+  return b->tiles_off + 4u * (size_t)(t > 0 ? t : 1) <= b->workspace_bytes;
+}
+
+// Rebuilds the tile map and the requests' first tiles for ipt and uploads
+// both (synchronises the stream: the host tables are temporaries).
+grng_status replan(grng_batch* b, int ipt, cudaStream_t stream) {
+  if (ipt == b->ipt) return GRNG_OK;
+  const int64_t tile_groups = (int64_t)kThreads * ipt;
+  const int64_t tiles = tiles_at(b, ipt);
+  std::vector<int32_t> tile_req((size_t)(tiles > 0 ? tiles : 1), 0);
+  std::vector<BatchReq> h = b->host_reqs;
+  int64_t t = 0;
+  for (int32_t i = 0; i < b->count; ++i) {
+    h[i].first_tile = t;
+    const int64_t nt = (b->groups[i] + tile_groups - 1) / tile_groups;
+    for (int64_t k = 0; k < nt; ++k) tile_req[(size_t)(t + k)] = i;
+    t += nt;
+  }
+  // the offsets are not touched: the device copy is the live one
+  char* ws = reinterpret_cast<char*>(b->workspace);
+  cudaError_t err = cudaMemcpyAsync(ws + b->reqs_off, h.data(), sizeof(BatchReq) * h.size(),
+                                    cudaMemcpyHostToDevice, stream);
+  if (err == cudaSuccess && tiles > 0)
+    err = cudaMemcpyAsync(ws + b->tiles_off, tile_req.data(), 4u * (size_t)tiles,
+                          cudaMemcpyHostToDevice, stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+  if (err != cudaSuccess) {
+    set_error("batch re-plan upload failed: %s", cudaGetErrorString(err));
+    cudaGetLastError();
+    return GRNG_ERR_CUDA;
+  }
+  b->host_reqs = std::move(h);
+  b->ipt = ipt;
+  b->tiles = tiles;
+  return GRNG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+grng_status grng_batch_set_config(grng_batch_t b, int32_t ipt, int32_t ctas_per_sm,
+                                  grng_stream_t stream) {
+  if (b == nullptr || ctas_per_sm < 1 || ctas_per_sm > 32 || ipt < 1 || ipt > 64) {
+    set_error("bad batch, ipt (1..64) or ctas_per_sm (1..32)");
     return GRNG_ERR_INVALID_ARG;
   }
+  if (!fits(b, ipt)) {
+    set_error("the tile map at %d groups per thread does not fit the batch's workspace", ipt);
+    return GRNG_ERR_INVALID_ARG;
+  }
+  const grng_status st = replan(b, ipt, (cudaStream_t)stream);
+  if (st != GRNG_OK) return st;
   b->ctas_per_sm = ctas_per_sm;
   return GRNG_OK;
 }
@@ -549,14 +617,15 @@ grng_status grng_batch_launch(grng_batch_t b, grng_stream_t stream) {
   return batch_enqueue(b, (cudaStream_t)stream, true);
 }
 
-grng_status grng_batch_autotune(grng_batch_t b, grng_stream_t stream_in, int32_t* best_ctas,
-                                float* best_ms) {
+grng_status grng_batch_autotune(grng_batch_t b, grng_stream_t stream_in, int32_t* best_ipt,
+                                int32_t* best_ctas, float* best_ms) {
   if (b == nullptr) {
     set_error("batch is NULL");
     return GRNG_ERR_INVALID_ARG;
   }
   cudaStream_t stream = (cudaStream_t)stream_in;
-  const int32_t cands[] = {1, 2, 4, 6, 8, 12, 16};
+  const int32_t ipts[] = {1, 2, 4, 8, 16, 32};
+  const int32_t ctas[] = {1, 2, 4, 6, 8, 12, 16};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     set_error("event creation failed");
@@ -564,32 +633,42 @@ grng_status grng_batch_autotune(grng_batch_t b, grng_stream_t stream_in, int32_t
     return GRNG_ERR_CUDA;
   }
   float best = 1e30f;
-  int32_t arg = b->ctas_per_sm;
+  int32_t arg_ipt = b->ipt, arg_ctas = b->ctas_per_sm;
   grng_status st = GRNG_OK;
-  for (int32_t c : cands) {
-    b->ctas_per_sm = c;
-    // tuning fills do not advance the offsets: they rewrite the same outputs
-    if ((st = batch_enqueue(b, stream, false)) != GRNG_OK) break;
-    cudaEventRecord(e0, stream);
-    for (int k = 0; k < 3; ++k)
+  for (int32_t ipt : ipts) {
+    if (!fits(b, ipt)) continue;  // a workspace sized for larger tiles
+    if ((st = replan(b, ipt, stream)) != GRNG_OK) break;
+    for (int32_t c : ctas) {
+      b->ctas_per_sm = c;
+      // tuning fills do not advance the offsets: they rewrite the same outputs
       if ((st = batch_enqueue(b, stream, false)) != GRNG_OK) break;
-    cudaEventRecord(e1, stream);
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
-      st = GRNG_ERR_CUDA;
-      break;
+      cudaEventRecord(e0, stream);
+      for (int k = 0; k < 3 && st == GRNG_OK; ++k) st = batch_enqueue(b, stream, false);
+      cudaEventRecord(e1, stream);
+      if (st != GRNG_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        set_error("batch autotune: timing failed");
+        cudaGetLastError();
+        st = GRNG_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / 3 < best) {
+        best = ms / 3;
+        arg_ipt = ipt;
+        arg_ctas = c;
+      }
     }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms / 3 < best) {
-      best = ms / 3;
-      arg = c;
-    }
+    if (st != GRNG_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->ctas_per_sm = arg;
+  if (st == GRNG_OK) st = replan(b, arg_ipt, stream);
+  b->ctas_per_sm = arg_ctas;
   if (st != GRNG_OK) return st;
-  if (best_ctas) *best_ctas = arg;
+  if (best_ipt) *best_ipt = arg_ipt;
+  if (best_ctas) *best_ctas = arg_ctas;
   if (best_ms) *best_ms = best;
   return GRNG_OK;
 }

@@ -207,7 +207,7 @@ GRNG_BM_HD void neg_log(uint64_t m1, uint64_t& lm, int& le) {
   uint64_t M;
   uint32_t e;
   if (m1h != 0) {
-    const uint32_t s = 31u - (uint32_t)ilog2_small(m1h);  // clz(m1h), 11..31 (m1h < 2^21)
+    const uint32_t s = clz32(m1h);          // 11..31 (m1h < 2^21)
     M = join(shl_hi(m1l, m1h, s), m1l << s);
     e = s - 11u;
   } else {
@@ -269,7 +269,7 @@ GRNG_BM_HD void neg_log(uint64_t m1, uint64_t& lm, int& le) {
   }
   // Lf >= 2^54 (-ln u1 >= ln c_1 > 2^-10 here), so its high word is not 0
   const uint32_t Lh = (uint32_t)(Lf >> 32), Ll = (uint32_t)Lf;
-  const uint32_t nz = 22u - (uint32_t)ilog2_small(Lh >> 9);  // clz(Lh), 0..10 (Lh >= 2^22)
+  const uint32_t nz = clz32(Lh);            // 0..9 (Lh >= 2^22)
   lm = join(shl_hi(Ll, Lh, nz), Ll << nz);
   le = lb - (int)nz;
 }
@@ -358,11 +358,7 @@ GRNG_BM_HD void sincos_turns(uint64_t x2, uint64_t& c_abs, bool& c_neg, uint64_t
 GRNG_BM_HD double assemble(uint64_t p, int k, bool neg) {
   const uint32_t ph = (uint32_t)(p >> 32), pl = (uint32_t)p;
   uint32_t mh, ml, s;
-  if (ph >= 256u) {                                 // clz(ph) from the float exponent
-    s = 23u - (uint32_t)ilog2_small(ph >> 8);
-    mh = shl_hi(pl, ph, s);
-    ml = pl << s;
-  } else if (ph != 0) {                             // p < 2^40 (rare)
+  if (ph != 0) {
     s = clz32(ph);
     mh = shl_hi(pl, ph, s);
     ml = pl << s;

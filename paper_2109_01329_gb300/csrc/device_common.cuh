@@ -39,6 +39,33 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The ten round keys of one key, (k0 + r W0, k1 + r W1) for r = 0..9, made
+// once per launch on the host.  Kept in a kernel's parameter space, each
+// round's key is a constant-bank operand of its XOR, so the key schedule
+// costs no instruction in the loop.
+struct PhiloxRoundKeys {
+  uint32_t k[20];
+};
+__host__ __device__ inline PhiloxRoundKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+  PhiloxRoundKeys rk;
+  for (int r = 0; r < 10; ++r) {
+    rk.k[2 * r] = k0 + (uint32_t)r * kPhiloxW0;
+    rk.k[2 * r + 1] = k1 + (uint32_t)r * kPhiloxW1;
+  }
+  return rk;
+}
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxRoundKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+    const uint32_t lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+    const uint32_t lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ rk.k[2 * r], lo1, hi0 ^ c.w ^ rk.k[2 * r + 1], lo0);
+  }
+  return c;
+}
+
 // Philox counter of a block index given as (lo, hi) 64-bit halves.  Word
 // offsets live in Z / 2^128, so block indices live in Z / 2^126: the top two
 // bits are cleared, which makes word 2^128 + g equal to word g.
@@ -88,18 +115,21 @@ __device__ __forceinline__ uint64_t u53(uint32_t wa, uint32_t wb) {
 
 // The FP64 uniform x 2^-53, x = u53(w_a, w_b), in 32-bit halves.  Unless
 // x < 2^32 (probability 2^-21) the leading one of x lies in its top 21 bits
-// h = w_a >> 11: with s = clz(h) - 11, m = x << s has it at bit 52 and
-// x 2^-53 = m 2^(-53 - s), whose bit pattern is m + (1021 - s) 2^52 (the
-// leading one of m adds the missing 1 to the biased exponent 1022 - s).
-// Same value as scaled_u54_to_f64(x, -53); about a third of its operations.
+// h = w_a >> 11: with c = clz(h) and s = c - 11, m = x << s has it at bit 52
+// and x 2^-53 = m 2^(-53 - s), whose bit pattern is m + (1021 - s) 2^52 =
+// m + (1032 - c) 2^52 (the leading one of m adds the missing 1 to the biased
+// exponent 1022 - s).  The leading-zero count runs on the special-function
+// pipe, which the uniform fills leave idle, in place of four integer and
+// FP32 operations.  Same value as scaled_u54_to_f64(x, -53).
 __device__ __forceinline__ double u01_f64(uint32_t wa, uint32_t wb) {
   const uint32_t h = wa >> 11;
   const uint32_t l = __funnelshift_r(wb, wa, 11);  // low 32 bits of x
   if (h == 0) return scaled_u54_to_f64((uint64_t)l, -53);
-  const uint32_t s = 20u - (uint32_t)bm64::ilog2_small(h);  // clz(h) - 11, 0..20 (h < 2^21)
+  const uint32_t c = (uint32_t)__clz((int)h);      // 11..31
+  const uint32_t s = c - 11u;                      // 0..20
   const uint32_t mh = __funnelshift_l(l, h, s);    // high half of x << s
   const uint32_t ml = l << s;
-  return __hiloint2double((int)(mh + ((1021u - s) << 20)), (int)ml);
+  return __hiloint2double((int)(mh + (1032u << 20) - (c << 20)), (int)ml);
 }
 
 // ---------------------------------------------------------- range transform

@@ -132,4 +132,9 @@ void set_error(const char* fmt, ...);
 // Multiprocessor count of the current device (cached per device).
 int current_device_sms(int* device_out);
 
+// Tuned launch geometry of a fill of n elements (tune.cpp): Philox4x32-10,
+// the cap on resident CTAs per SM; MRG32k3a, threads per SM of the chunk
+// plan in units of 256; 0 = the launcher's built-in choice.
+int32_t fill_geometry(int engine_kind, int variant, int64_t n);
+
 }  // namespace grng

@@ -369,8 +369,10 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
                        (phase_w % (uint32_t)I::wpu) == 0;
   p.head_units = aligned ? (int64_t)(phase_w / I::wpu) : 0;
 
-  // About one resident wave of threads, one chunk each.
-  const int64_t target_threads = (int64_t)sms * 2048;
+  // About one resident wave of threads, one chunk each (2048 threads per SM,
+  // or the tuned count).
+  const int32_t geom = fill_geometry(GRNG_MRG32K3A, V, r.n * r.num_streams);
+  const int64_t target_threads = (int64_t)sms * (geom > 0 ? 256 * (int64_t)geom : 2048);
   int64_t per_stream_threads = target_threads / r.num_streams;
   if (per_stream_threads < 1) per_stream_threads = 1;
   const int64_t span = p.units + p.head_units;

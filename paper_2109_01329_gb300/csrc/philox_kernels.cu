@@ -80,14 +80,14 @@ struct StreamParams {
   int64_t edge[2];    // partial groups, or -1
   uint64_t base_lo;   // block counter of group 0
   uint64_t base_hi;
-  uint32_t k0, k1;
+  PhiloxRoundKeys rk;
 };
 
 template <int V, bool kHiUniform>
 __device__ __forceinline__ uint4 group_block(const StreamParams& p, uint64_t j) {
   const uint64_t lo = p.base_lo + j;
   const uint64_t hi = kHiUniform ? p.base_hi : p.base_hi + ((lo < p.base_lo) ? 1u : 0u);
-  return philox4x32_10(ctr_from(lo, hi), p.k0, p.k1);
+  return philox4x32_10(ctr_from(lo, hi), p.rk);
 }
 
 template <int V, int U, bool kHiUniform>
@@ -138,12 +138,12 @@ constexpr bool stream_wants_5_ctas() {
 }
 
 template <int V, int U, bool kHiUniform>
-__global__ void __launch_bounds__(kThreads) philox_stream_kernel(const StreamParams p) {
+__global__ void __launch_bounds__(kThreads) philox_stream_kernel(const __grid_constant__ StreamParams p) {
   philox_stream_body<V, U, kHiUniform>(p);
 }
 
 template <int V, int U, bool kHiUniform>
-__global__ void __launch_bounds__(kThreads, 5) philox_stream_kernel_5(const StreamParams p) {
+__global__ void __launch_bounds__(kThreads, 5) philox_stream_kernel_5(const __grid_constant__ StreamParams p) {
   philox_stream_body<V, U, kHiUniform>(p);
 }
 
@@ -173,7 +173,7 @@ struct ShiftParams {
   uint64_t base_lo;   // block holding the first word of (virtual) group 0
   uint64_t base_hi;
   uint32_t ph;        // its word phase: 1..3, or 0..3 with kSplit
-  uint32_t k0, k1;
+  PhiloxRoundKeys rk;
 };
 
 template <bool kSplit>
@@ -197,7 +197,7 @@ __device__ __forceinline__ void philox_shift_body(const ShiftParams& p) {
       const uint64_t j = (uint64_t)((c + u * TW) * kPer + lane);
       const uint64_t lo = p.base_lo + j;
       const uint64_t hi = kHiUniform ? p.base_hi : p.base_hi + ((lo < p.base_lo) ? 1u : 0u);
-      b[u] = philox4x32_10(ctr_from(lo, hi), p.k0, p.k1);
+      b[u] = philox4x32_10(ctr_from(lo, hi), p.rk);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -237,12 +237,12 @@ __device__ __forceinline__ void philox_shift_body(const ShiftParams& p) {
 }
 
 template <int V, int U, bool kHiUniform, bool kSplit>
-__global__ void __launch_bounds__(kThreads) philox_shift_kernel(const ShiftParams p) {
+__global__ void __launch_bounds__(kThreads) philox_shift_kernel(const __grid_constant__ ShiftParams p) {
   philox_shift_body<V, U, kHiUniform, kSplit>(p);
 }
 
 template <int V, int U, bool kHiUniform, bool kSplit>
-__global__ void __launch_bounds__(kThreads, 5) philox_shift_kernel_5(const ShiftParams p) {
+__global__ void __launch_bounds__(kThreads, 5) philox_shift_kernel_5(const __grid_constant__ ShiftParams p) {
   philox_shift_body<V, U, kHiUniform, kSplit>(p);
 }
 
@@ -258,11 +258,11 @@ struct MultiParams {
   uint64_t sb_lo, sb_hi;      // block-counter stride between streams
   int64_t tq, tr;             // grid stride = tq * groups + tr
   uint64_t tqsb_lo, tqsb_hi;  // tq * sb
-  uint32_t k0, k1;
+  PhiloxRoundKeys rk;
 };
 
 template <int V>
-__global__ void __launch_bounds__(kThreads) philox_multi_kernel(const MultiParams p) {
+__global__ void __launch_bounds__(kThreads) philox_multi_kernel(const __grid_constant__ MultiParams p) {
   const int64_t T = (int64_t)gridDim.x * kThreads;
   int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (idx >= p.total) return;
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kThreads) philox_multi_kernel(const MultiParam
   for (; idx < p.total; idx += T) {
     uint64_t c_lo = sb_lo, c_hi = sb_hi;
     add128(c_lo, c_hi, (uint64_t)j, 0);
-    p.out[idx] = block_outputs<V>(philox4x32_10(ctr_from(c_lo, c_hi), p.k0, p.k1), p.t);
+    p.out[idx] = block_outputs<V>(philox4x32_10(ctr_from(c_lo, c_hi), p.rk), p.t);
     j += p.tr;
     add128(sb_lo, sb_hi, p.tqsb_lo, p.tqsb_hi);
     if (j >= p.groups) {
@@ -294,7 +294,7 @@ struct StagedParams {
   int64_t tiles_per_stream;  // tiles of kThreads groups
   uint64_t off_lo, off_hi;   // word offset of stream 0
   uint64_t stride_lo, stride_hi;
-  uint32_t k0, k1;
+  PhiloxRoundKeys rk;
 };
 
 // Blocks per tile: 256 groups are 1024 words, plus up to 3 words of a unit
@@ -302,7 +302,7 @@ struct StagedParams {
 constexpr int kTileBlocks = kThreads + 4;
 
 template <int V>
-__global__ void __launch_bounds__(kThreads) philox_staged_kernel(const StagedParams p) {
+__global__ void __launch_bounds__(kThreads) philox_staged_kernel(const __grid_constant__ StagedParams p) {
   using I = VInfo<V>;
   constexpr int kEpg = 16 / I::es;
   constexpr int kWpu = I::wpu;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kThreads) philox_staged_kernel(const StagedPar
     for (int i = threadIdx.x; i < nblocks; i += kThreads) {
       uint64_t c_lo = b_lo, c_hi = b_hi;
       add128(c_lo, c_hi, (uint64_t)i, 0);
-      sblocks[i] = philox4x32_10(ctr_from(c_lo, c_hi), p.k0, p.k1);
+      sblocks[i] = philox4x32_10(ctr_from(c_lo, c_hi), p.rk);
     }
     __syncthreads();
 
@@ -379,6 +379,10 @@ __global__ void __launch_bounds__(kThreads) philox_staged_kernel(const StagedPar
   }
 }
 
+// Resident CTAs per SM a launch may use: the occupancy, capped by the tuned
+// geometry when one is set.
+int ctas_cap(int occ, int32_t geom) { return geom > 0 && geom < occ ? (int)geom : occ; }
+
 template <typename K>
 int blocks_per_sm(K kernel) {
   int b = 0;
@@ -393,7 +397,7 @@ int blocks_per_sm(K kernel) {
 // Launches the shift kernel: words of (virtual) group 0 start at word a of
 // the stream (128-bit, a = off - head words, one element earlier for kSplit).
 template <int V, bool kSplit>
-void launch_shift(ShiftParams& p, uint64_t a_lo, uint64_t a_hi, int sms,
+void launch_shift(ShiftParams& p, uint64_t a_lo, uint64_t a_hi, int sms, int32_t geom,
                   cudaStream_t stream) {
   constexpr int kPer = shift_per_warp<kSplit>();
   constexpr int kU = blocks_per_thread<V>();
@@ -420,14 +424,14 @@ void launch_shift(ShiftParams& p, uint64_t a_lo, uint64_t a_hi, int sms,
   const int64_t warps = (p.chunks + kU - 1) / kU;
   int64_t grid = (warps + (kThreads / 32) - 1) / (kThreads / 32);
   if (grid < 1) grid = 1;
-  const int64_t cap = (int64_t)sms * o;
+  const int64_t cap = (int64_t)sms * ctas_cap(o, geom);
   if (grid > cap) grid = cap;
   // blocks touched: below (chunks + kU * warps in flight) * kPer + 32 past base
   const uint64_t reach =
       (uint64_t)(p.chunks + (int64_t)kU * grid * (kThreads / 32) + 1) * (uint64_t)kPer + 64u;
   const bool hi_uniform = p.base_lo + reach >= p.base_lo;
   if (!hi_uniform) {
-    const int64_t cap2 = (int64_t)sms * occ[1].load(std::memory_order_relaxed);
+    const int64_t cap2 = (int64_t)sms * ctas_cap(occ[1].load(std::memory_order_relaxed), geom);
     if (grid > cap2) grid = cap2;
   }
   (hi_uniform ? k_uni : k_carry)<<<(unsigned)grid, kThreads, 0, stream>>>(p);
@@ -439,6 +443,7 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
   constexpr int kEpg = 16 / I::es;
   int dev = 0;
   const int sms = current_device_sms(&dev);
+  const int32_t geom = fill_geometry(GRNG_PHILOX4X32X10, V, r.n * r.num_streams);
   const uintptr_t addr = (uintptr_t)r.out;
   const uint32_t phase_w = (uint32_t)((addr & 15u) / 4u);  // output words before out in group 0
   const uint64_t stream_bytes = (uint64_t)r.n * I::es;
@@ -464,8 +469,7 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.head = head;
     p.base_lo = base_lo;
     p.base_hi = base_hi;
-    p.k0 = r.key[0];
-    p.k1 = r.key[1];
+    p.rk = philox_round_keys(r.key[0], r.key[1]);
     // full groups: the first group is partial when head > 0, the last one
     // when the end is not on a group boundary (or both are the same group)
     int64_t jf = head > 0 ? 1 : 0;
@@ -499,7 +503,7 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     const int64_t work = (jl - jf + (int64_t)kU - 1) / kU;
     int64_t grid = (work + kThreads - 1) / kThreads;
     if (grid < 1) grid = 1;
-    const int64_t cap = (int64_t)sms * o;
+    const int64_t cap = (int64_t)sms * ctas_cap(o, geom);
     if (grid > cap) grid = cap;
     kernel<<<(unsigned)grid, kThreads, 0, stream>>>(p);
   } else if (fast && head == 0 && (stream_bytes % 16u) == 0) {
@@ -512,8 +516,7 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.base_hi = base_hi;
     p.sb_lo = (r.stride_lo >> 2) | (r.stride_hi << 62);
     p.sb_hi = r.stride_hi >> 2;
-    p.k0 = r.key[0];
-    p.k1 = r.key[1];
+    p.rk = philox_round_keys(r.key[0], r.key[1]);
     static std::atomic<int> occ_cache{0};
     int occ = occ_cache.load(std::memory_order_relaxed);
     if (occ == 0) {
@@ -521,7 +524,7 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
       occ_cache.store(occ, std::memory_order_relaxed);
     }
     int64_t grid = (p.total + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)sms * occ;
+    const int64_t cap = (int64_t)sms * ctas_cap(occ, geom);
     if (grid > cap) grid = cap;
     const int64_t gstride = grid * kThreads;
     p.tq = gstride / p.groups;
@@ -542,16 +545,15 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.n = r.n;
     p.head = head;
     p.groups = groups;
-    p.k0 = r.key[0];
-    p.k1 = r.key[1];
+    p.rk = philox_round_keys(r.key[0], r.key[1]);
     if ((phase_w % (uint32_t)I::wpu) == 0) {
-      launch_shift<V, false>(p, lo0, hi0, sms, stream);
+      launch_shift<V, false>(p, lo0, hi0, sms, geom, stream);
     } else if constexpr (I::epu == 2) {
       // the virtual groups start one element (es / 4 words) earlier
       const uint32_t pv = phase_w + (uint32_t)(I::es / 4);
       const uint64_t a_lo = r.off_lo - pv;
       const uint64_t a_hi = r.off_hi - ((r.off_lo < pv) ? 1u : 0u);
-      launch_shift<V, true>(p, a_lo, a_hi, sms, stream);
+      launch_shift<V, true>(p, a_lo, a_hi, sms, geom, stream);
     }
   } else {
     StagedParams p;
@@ -566,8 +568,7 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.off_hi = r.off_hi;
     p.stride_lo = r.stride_lo;
     p.stride_hi = r.stride_hi;
-    p.k0 = r.key[0];
-    p.k1 = r.key[1];
+    p.rk = philox_round_keys(r.key[0], r.key[1]);
     static std::atomic<int> occ_cache{0};
     int occ = occ_cache.load(std::memory_order_relaxed);
     if (occ == 0) {
@@ -575,7 +576,7 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
       occ_cache.store(occ, std::memory_order_relaxed);
     }
     int64_t grid = p.num_streams * p.tiles_per_stream;
-    const int64_t cap = (int64_t)sms * occ;
+    const int64_t cap = (int64_t)sms * ctas_cap(occ, geom);
     if (grid > cap) grid = cap;
     philox_staged_kernel<V><<<(unsigned)grid, kThreads, 0, stream>>>(p);
   }

@@ -9,6 +9,21 @@
 //     FP64 Box-Muller.  Two chain shapes, the faster one counts: 8
 //     independent chains by a constant multiplier (as in a Philox round), and
 //     4 chains whose multiplier is the neighbouring chain's value.
+//   grng_probe_op_rate: operations per second of one of the method-level
+//     operations below, evaluated with CUDA's own math library on inputs from
+//     a per-thread linear congruential sequence (one 32-bit multiply-add per
+//     input), several independent chains per thread, every SM busy:
+//       0  FP32 Box-Muller pair: sqrtf(-2 logf(u1)) times sincospif(2 u2)
+//       1  FP32 expf
+//       2  FP32 normcdfinvf (the inverse-CDF method's Phi^-1)
+//       3  FP64 Box-Muller pair: sqrt(-2 log(u1)) times sincospi(2 u2)
+//       4  FP64 fused multiply-add (the FP64 pipe alone)
+//       5  FP32 fused multiply-add
+//       6  special-function unit: lg2.approx.ftz.f32
+//       7  FP64 normcdfinv
+//     These are the ceilings of the transcendental fills: how fast this GPU's
+//     math library evaluates the method's operations, without generating
+//     words or writing memory.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -59,7 +74,113 @@ __global__ void __launch_bounds__(256) probe_mulwide_cross(uint32_t* sink, int i
   if ((a0 ^ a1 ^ a2 ^ a3) == 0x9E3779B9u) sink[0] = a0;  // keeps the chains alive
 }
 
+__device__ __forceinline__ uint32_t lcg(uint32_t x) { return x * 1664525u + 1013904223u; }
+__device__ __forceinline__ float u_open_f32(uint32_t x) {  // (0, 1]
+  return (float)((x >> 8) + 1u) * 0x1p-24f;
+}
+__device__ __forceinline__ double u_open_f64(uint32_t x) {
+  return (double)((x >> 8) + 1u) * 0x1p-24;
+}
+
+constexpr int kOpChains = 4;
+
+// Each thread runs kOpChains independent chains for iters steps; every step
+// is one operation of the kind (a pair for the Box-Muller kinds).
+template <int K>
+__global__ void __launch_bounds__(256) probe_op(float* sink, int iters, uint32_t seed) {
+  uint32_t x[kOpChains];
+  float accf[kOpChains];
+  double accd[kOpChains];
+#pragma unroll
+  for (int k = 0; k < kOpChains; ++k) {
+    x[k] = seed + (blockIdx.x * 256u + threadIdx.x) * 977u + (uint32_t)k * 131u;
+    accf[k] = 0.f;
+    accd[k] = 0.0;
+  }
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kOpChains; ++k) {
+      if constexpr (K != 4 && K != 5) x[k] = lcg(x[k]);
+      if constexpr (K == 0) {
+        const uint32_t y = lcg(x[k]);
+        const float rho = sqrtf(-2.0f * logf(u_open_f32(x[k])));
+        float s, c;
+        sincospif(2.0f * ((float)(y >> 8) * 0x1p-24f), &s, &c);
+        accf[k] += rho * c + rho * s;
+      } else if constexpr (K == 1) {
+        accf[k] += expf(u_open_f32(x[k]) * 8.0f - 4.0f);
+      } else if constexpr (K == 2) {
+        accf[k] += normcdfinvf(u_open_f32(x[k]) * 0.999999f);
+      } else if constexpr (K == 3) {
+        const uint32_t y = lcg(x[k]);
+        const double rho = sqrt(-2.0 * log(u_open_f64(x[k])));
+        double s, c;
+        sincospi(2.0 * ((double)(y >> 8) * 0x1p-24), &s, &c);
+        accd[k] += rho * c + rho * s;
+      } else if constexpr (K == 4) {
+        accd[k] = fma(accd[k], 0.999999999, 1e-9);
+      } else if constexpr (K == 5) {
+        accf[k] = fmaf(accf[k], 0.9999f, 1e-4f);
+      } else if constexpr (K == 6) {
+        float l;
+        asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(u_open_f32(x[k])));
+        accf[k] += l;
+      } else {
+        accd[k] += normcdfinv(u_open_f64(x[k]) * 0.999999);
+      }
+    }
+  }
+  float t = 0.f;
+  double td = 0.0;
+#pragma unroll
+  for (int k = 0; k < kOpChains; ++k) {
+    t += accf[k];
+    td += accd[k];
+  }
+  if (t == 1234.5f || td == 1234.5) sink[0] = t + (float)td;  // keeps the chains alive
+}
+
 }  // namespace
+
+extern "C" __attribute__((visibility("default"))) int grng_probe_op_rate(void* dev_sink, int kind,
+                                                                           double* per_s) {
+  if (kind < 0 || kind > 7 || per_s == nullptr) return 1;
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 4;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // about a millisecond or more per launch at the expected rates
+  static const int kIters[8] = {64, 128, 64, 8, 1024, 4096, 2048, 8};
+  const int iters = kIters[kind];
+  const int grid = sms * 8;
+  float* sink = (float*)dev_sink;
+  auto launch = [&](uint32_t seed) {
+    switch (kind) {
+      case 0: probe_op<0><<<grid, 256>>>(sink, iters, seed); break;
+      case 1: probe_op<1><<<grid, 256>>>(sink, iters, seed); break;
+      case 2: probe_op<2><<<grid, 256>>>(sink, iters, seed); break;
+      case 3: probe_op<3><<<grid, 256>>>(sink, iters, seed); break;
+      case 4: probe_op<4><<<grid, 256>>>(sink, iters, seed); break;
+      case 5: probe_op<5><<<grid, 256>>>(sink, iters, seed); break;
+      case 6: probe_op<6><<<grid, 256>>>(sink, iters, seed); break;
+      default: probe_op<7><<<grid, 256>>>(sink, iters, seed); break;
+    }
+  };
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  launch(1u);
+  const int reps = 3;
+  cudaEventRecord(a);
+  for (int i = 0; i < reps; ++i) launch(2u + (uint32_t)i);
+  cudaEventRecord(b);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *per_s = (double)grid * 256.0 * iters * kOpChains * reps / (ms * 1e-3);
+  return cudaGetLastError() == cudaSuccess ? 0 : 4;
+}
 
 extern "C" __attribute__((visibility("default"))) int grng_probe_write_gbs(void* dev_buf,
                                                                              int64_t bytes,

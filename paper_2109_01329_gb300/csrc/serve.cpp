@@ -16,7 +16,9 @@
 //     arriving;
 //   * the host callback stamps each request complete (latency = completion -
 //     arrival) and frees its slot; outputs stay in the pool until released
-//     (or at once with GRNG_SERVE_AUTO_RELEASE).
+//     (or, with GRNG_SERVE_AUTO_RELEASE, at completion plus the release
+//     delay: a consumer that keeps each output that long, which makes the
+//     budget bind when outputs arrive faster than they are let go).
 // No call allocates device memory: the pool and every table live in the
 // caller's buffer; pinned staging for the tables is allocated at creation.
 #include <cuda_runtime.h>
@@ -101,7 +103,7 @@ struct Req {
   int64_t tiles = 0;
   size_t off = 0;                     // pool offset of the output
   int state = 0;                      // 0 queued, 1 launched, 2 done
-  Clock::time_point t_arrival, t_done;
+  Clock::time_point t_arrival, t_admit, t_done;
 };
 
 struct Slot {
@@ -139,8 +141,12 @@ struct grng_server {
   bool stop = false;
   std::thread sched;
   cudaError_t async_error = cudaSuccess;
+  // automatic releases waiting for their time: deadline -> (offset, bytes)
+  int64_t release_delay_us = 0;
+  std::multimap<Clock::time_point, std::pair<size_t, size_t>> deferred;
   // statistics
   std::vector<double> lat_us;
+  std::vector<double> wait_us;  // arrival to admission
   int64_t submitted = 0, completed = 0, rejected = 0, samples = 0, batches = 0,
           batch_reqs = 0;
   size_t peak_used = 0;
@@ -167,7 +173,11 @@ void CUDART_CB on_batch_done(void* arg) {
       S->samples += r.samples;
       S->t_last = now;
       if (S->flags & GRNG_SERVE_AUTO_RELEASE) {
-        S->alloc.release(r.off, r.bytes);
+        if (S->release_delay_us > 0)
+          S->deferred.emplace(now + std::chrono::microseconds(S->release_delay_us),
+                              std::make_pair(r.off, r.bytes));
+        else
+          S->alloc.release(r.off, r.bytes);
         S->reqs.erase(it);
       }
     }
@@ -178,11 +188,29 @@ void CUDART_CB on_batch_done(void* arg) {
   S->cv_done.notify_all();
 }
 
+// Frees the automatic releases whose time has come (caller holds S->mu).
+void release_due(grng_server* S) {
+  const Clock::time_point now = Clock::now();
+  while (!S->deferred.empty() && S->deferred.begin()->first <= now) {
+    S->alloc.release(S->deferred.begin()->second.first, S->deferred.begin()->second.second);
+    S->deferred.erase(S->deferred.begin());
+  }
+}
+
+// Waits for a submission, a completion or the next automatic release.
+void wait_for_work(grng_server* S, std::unique_lock<std::mutex>& lk) {
+  if (S->deferred.empty())
+    S->cv.wait(lk);
+  else
+    S->cv.wait_until(lk, S->deferred.begin()->first);
+}
+
 void scheduler(grng_server* S) {
   std::unique_lock<std::mutex> lk(S->mu);
   std::vector<PartDesc> parts;
   parts.reserve(kMaxParts);
   for (;;) {
+    release_due(S);
     Slot* slot = nullptr;
     for (int i = 0; i < S->num_slots; ++i)
       if (!S->slots[i].busy) {
@@ -191,13 +219,14 @@ void scheduler(grng_server* S) {
       }
     if (S->stop) break;  // requests not yet launched are abandoned
     if (slot == nullptr || S->queue.empty()) {
-      S->cv.wait(lk);
+      wait_for_work(S, lk);
       continue;
     }
     // admit in arrival order while the outputs fit the budget
     std::vector<uint64_t> batch;
     int nparts = 0;
     int64_t ntiles = 0;
+    const Clock::time_point t_admit = Clock::now();
     while (!S->queue.empty()) {
       Req& r = S->reqs[S->queue.front()];
       if (nparts + r.spec.num_parts > kMaxParts) break;
@@ -206,13 +235,16 @@ void scheduler(grng_server* S) {
       if (!S->alloc.alloc(r.bytes, &off)) break;
       r.off = off;
       r.state = 1;
+      r.t_admit = t_admit;
+      S->wait_us.push_back(
+          std::chrono::duration<double, std::micro>(t_admit - r.t_arrival).count());
       batch.push_back(S->queue.front());
       S->queue.pop_front();
       nparts += r.spec.num_parts;
       ntiles += r.tiles;
     }
     if (batch.empty()) {  // the oldest request waits for space
-      S->cv.wait(lk);
+      wait_for_work(S, lk);
       continue;
     }
     S->peak_used = std::max(S->peak_used, S->alloc.used());
@@ -522,6 +554,30 @@ grng_status grng_server_stats(grng_server_t S, grng_serve_stats* out) {
     out->latency_max_us = lat.back();
     out->latency_mean_us = sum / (double)lat.size();
   }
+  std::vector<double> w = S->wait_us;
+  if (!w.empty()) {
+    std::sort(w.begin(), w.end());
+    auto pct = [&](double q) {
+      size_t i = (size_t)(q / 100.0 * (double)(w.size() - 1) + 0.5);
+      return w[std::min(i, w.size() - 1)];
+    };
+    out->admit_wait_p50_us = pct(50);
+    out->admit_wait_p99_us = pct(99);
+    out->admit_wait_max_us = w.back();
+  }
+  return GRNG_OK;
+}
+
+grng_status grng_server_set_release_delay(grng_server_t S, int64_t delay_us) {
+  if (S == nullptr || delay_us < 0) {
+    set_error("server NULL or delay < 0");
+    return GRNG_ERR_INVALID_ARG;
+  }
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    S->release_delay_us = delay_us;
+  }
+  S->cv.notify_all();
   return GRNG_OK;
 }
 
@@ -532,6 +588,7 @@ grng_status grng_server_reset_stats(grng_server_t S) {
   }
   std::lock_guard<std::mutex> g(S->mu);
   S->lat_us.clear();
+  S->wait_us.clear();
   S->submitted = S->completed = S->rejected = S->samples = S->batches = S->batch_reqs = 0;
   S->peak_used = S->alloc.used();
   S->have_first = false;

@@ -225,3 +225,37 @@ def test_host_wrappers_refuse_n_beyond_the_tensor(g):
     with pytest.raises(ValueError):
         g.generate_host_static(d, e, host, n=-1)
     assert e.offset == 0
+
+
+def test_tune_table_save_load_reset(g, tmp_path):
+    """The launch-geometry table: set, save, reset, load back; bad files and
+    bad arguments are refused (no GPU work involved)."""
+    d32 = g.Distribution.uniform(0.0, 1.0, g.F32)
+    d64 = g.Distribution.gaussian(0.0, 1.0, g.F64)
+    g.tune_reset()
+    assert g.fill_geometry(0, d32, 10**9) == 0
+    assert g.fill_geometry(0, d32, 10**9, 4) == 4
+    assert g.fill_geometry(1, d64, 1000, 12) == 12
+    # same bucket (bit length) shares the entry; another bucket does not
+    assert g.fill_geometry(0, d32, 2**29 + 1) == 4
+    assert g.fill_geometry(0, d32, 2**31) == 0
+    path = str(tmp_path / "tune.txt")
+    g.tune_save(path)
+    text = open(path).read().split("\n")
+    assert text[0] == "grng-tune 1" and len([x for x in text[1:] if x]) == 2
+    g.tune_reset()
+    assert g.fill_geometry(0, d32, 10**9) == 0
+    g.tune_load(path)
+    assert g.fill_geometry(0, d32, 10**9) == 4 and g.fill_geometry(1, d64, 1000) == 12
+    bad = tmp_path / "bad.txt"
+    bad.write_text("grng-tune 1\n0 99 3 4\n")
+    with pytest.raises(g.GrngError):
+        g.tune_load(str(bad))
+    bad.write_text("something else\n")
+    with pytest.raises(g.GrngError):
+        g.tune_load(str(bad))
+    with pytest.raises(g.GrngError):
+        g.fill_geometry(0, d32, 100, 65)
+    with pytest.raises(g.GrngError):
+        g.fill_geometry(2, d32, 100, 1)
+    g.tune_reset()

@@ -154,8 +154,8 @@ def test_autotune_keeps_outputs(g):
     # rewind: a fresh identical batch tuned then launched once
     reqs2 = _clone_requests(g, reqs)
     b2 = g.Batch(reqs2, ipt=1)
-    ctas, ms = b2.autotune()
-    assert 1 <= ctas <= 32 and ms > 0
+    ipt, ctas, ms = b2.autotune()
+    assert ipt in (1, 2, 4, 8, 16, 32) and 1 <= ctas <= 32 and ms > 0
     b2.launch()
     torch.cuda.synchronize()
     for x, r in zip(before, reqs2):
@@ -196,3 +196,37 @@ def test_4096_request_batch_equals_per_request(g, phased):
         m = min(q["n"], 4096)
         ref = oracle.generate(0, q["seed"], int(offs[int(i)]), kind, dtype, p0, p1, m)
         assert _close(kind, dtype, _host(reqs[int(i)][2][:m]), ref)
+
+
+def test_every_tuner_geometry_gives_the_same_outputs(g):
+    """The output is a function of the word index only, so every launch
+    geometry the autotuner tries (ipt x CTAs per SM) must give the outputs of
+    the same grng_generate calls; each launch continues every sequence."""
+    reqs, meta, _ = _mixed_requests(g, seed=9, count=40)
+    refs = _clone_requests(g, reqs)
+    b = g.Batch(reqs, ipt=8)  # workspace sized for ipt = 1: every ipt fits
+    for ipt in (1, 2, 4, 8, 16, 32):
+        for ctas in (1, 2, 4, 6, 8, 12, 16):
+            b.set_config(ipt, ctas)
+            b.launch()
+            torch.cuda.synchronize()
+            for (e, d, o, n), (er, dr, orf, nr) in zip(reqs, refs):
+                g.generate(dr, er, orf, n=nr)
+            torch.cuda.synchronize()
+            for k, ((e, d, o, n), (er, dr, orf, nr)) in enumerate(zip(reqs, refs)):
+                assert torch.equal(o[:n].view(torch.uint8), orf[:nr].view(torch.uint8)), \
+                    (ipt, ctas, k)
+    b.commit()
+    for (e, d, o, n), (er, dr, orf, nr) in zip(reqs, refs):
+        assert e.offset == er.offset
+
+
+def test_set_config_refuses_a_map_that_does_not_fit(g):
+    # 2^22 FP32 outputs are 2^20 groups: 4096 tiles at ipt 1, 512 at ipt 8
+    d = g.Distribution.uniform(0.0, 1.0)
+    reqs = [(g.Engine(0, 5, 0), d, torch.empty(1 << 22, dtype=torch.float32, device="cuda"),
+             1 << 22)]
+    b = g.Batch(reqs, ipt=8, tunable=False)
+    b.set_config(16, 4)  # larger tiles: a smaller map, fits
+    with pytest.raises(g.GrngError):
+        b.set_config(1, 4)

@@ -342,18 +342,55 @@ def test_copied_and_restored_engines_continue_the_sequence(g, engine_kind, seede
         def ref_at(off):
             return lambda k, dt, p0, p1, n: oracle.generate_words(engine_kind, words, off, k, dt,
                                                                   p0, p1, n)
-    # move the original mid-stream at an odd word phase
+    # move the original mid-stream at an odd word phase; offsets below are
+    # relative to the engine's start (a word-seeded Philox engine starts at
+    # word 4 * counter + 5)
+    start = e.offset
     _fill_check(g, e, engine_kind, var_a, 1001, ref_at(5), "original")
-    off = e.offset
-    assert off == 5 + 1002
+    rel = 5 + 1002
+    assert e.offset == start + 1002
     c = e.copy()
     r = g.Engine.restore(e.full_state)
     assert c.full_state == e.full_state == r.full_state
     n = 65537
     for eng, name in ((c, "copy"), (r, "restored"), (e, "original")):
-        _fill_check(g, eng, engine_kind, var_b, n, ref_at(off), name)
+        _fill_check(g, eng, engine_kind, var_b, n, ref_at(rel), name)
     # each advanced by its own call only
     for eng in (c, r, e):
-        assert eng.offset == off + 2 * n
-    _fill_check(g, c, engine_kind, var_a, 777, ref_at(off + 2 * n), "copy continues")
-    assert e.offset == off + 2 * n
+        assert eng.offset == start + 1002 + 2 * n
+    _fill_check(g, c, engine_kind, var_a, 777, ref_at(rel + 2 * n), "copy continues")
+    assert e.offset == start + 1002 + 2 * n
+
+
+@pytest.mark.parametrize("engine_kind", ENGINES)
+def test_every_fill_geometry_gives_the_same_outputs(g, engine_kind):
+    """Every launch geometry the fill autotuner tries gives the same words, bit
+    for bit (outputs depend on the word index only); after tuning, fills
+    still equal the oracle."""
+    cands = [0, 1, 2, 3, 4, 5, 6, 8] if engine_kind == 0 else [0, 1, 2, 4, 6, 12, 16]
+    g.tune_reset()
+    try:
+        for var in [VARIANTS[0], VARIANTS[4], VARIANTS[7], VARIANTS[10], VARIANTS[12]]:
+            _, kind, dtype, p0, p1 = var
+            d = g.Distribution(kind, dtype, p0, p1)
+            n = 1_000_003
+            outs = []
+            for geo in cands:
+                assert g.fill_geometry(engine_kind, d, n, geo) == geo
+                out = torch.empty(n, dtype=_torch_dtype(dtype), device="cuda")
+                g.generate(d, g.Engine(engine_kind, 2021, 5), out)
+                outs.append(out)
+            torch.cuda.synchronize()
+            for geo, o in zip(cands[1:], outs[1:]):
+                assert torch.equal(o.view(torch.uint8), outs[0].view(torch.uint8)), (var[0], geo)
+            buf = torch.empty(n, dtype=_torch_dtype(dtype), device="cuda")
+            geo, ms = g.fill_autotune(engine_kind, d, buf)
+            assert geo in cands and ms > 0
+            out = torch.empty(n, dtype=_torch_dtype(dtype), device="cuda")
+            g.generate(d, g.Engine(engine_kind, 2021, 5), out)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            ref = oracle.generate(engine_kind, 2021, 5, kind, dtype, p0, p1, n)
+            assert_parity(kind, dtype, got.view(np.uint32) if dtype == 0 else got, ref, var[0])
+    finally:
+        g.tune_reset()

@@ -127,3 +127,31 @@ def test_wait_times_out_then_completes(g):
         srv.wait(t, timeout_s=60.0)
         srv.release(t)
     srv.close()
+
+
+def test_held_outputs_make_the_budget_bind(g):
+    """Auto-released outputs held for a while after completion (a consumer
+    keeping each event's numbers) fill the budget: admission then waits for
+    held outputs to be let go, the pool never exceeds the budget, every
+    request completes, and the waits show in the admission statistics."""
+    budget = 8 << 20
+    srv = g.Server((3 * 1750 << 10) + budget, num_streams=3, auto_release=True)
+    srv.set_release_delay(0.05)
+    hits = [200_000] * 24  # 3.2 MB per event: about two fit at a time
+    t = np.arange(len(hits)) * 1e-4
+    srv.replay(t, [g.serve_request(300 + i, _event_parts(g, h)) for i, h in enumerate(hits)])
+    srv.drain(timeout_s=60)
+    st = srv.stats()
+    assert st["completed"] == len(hits) == st["submitted"]
+    assert st["peak_pool_bytes"] <= budget + (256 << 10)
+    # 24 events, two held at a time for 50 ms each: the last waits >= ~0.5 s
+    assert st["admit_wait_max_us"] > 3e5
+    assert st["admit_wait_p50_us"] <= st["admit_wait_p99_us"] <= st["admit_wait_max_us"]
+    time.sleep(0.1)
+    srv.set_release_delay(0.0)
+    # the held outputs went back to the budget: a 6.4 MB request fits again
+    srv.reset_stats()
+    srv.submit(g.serve_request(999, _event_parts(g, 400_000)))
+    srv.drain(timeout_s=30)
+    assert srv.stats()["completed"] == 1
+    srv.close()

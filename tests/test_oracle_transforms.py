@@ -69,6 +69,41 @@ def test_uniform_f32_interval_and_error_bound(a, b):
     assert r[0] == af
 
 
+def _round_f32(x: Fraction) -> float:
+    """x rounded to the nearest float32 (ties to even), exactly (normal range)."""
+    if x == 0:
+        return 0.0
+    e = math.floor(math.log2(abs(x)))
+    while Fraction(2) ** e > abs(x):
+        e -= 1
+    while Fraction(2) ** (e + 1) <= abs(x):
+        e += 1
+    ulp = Fraction(2) ** (e - 23)
+    return float(round(x / ulp) * ulp)
+
+
+@pytest.mark.parametrize("a,b", [(-1e3, 7.0), (2.5, 3.75), (1e-3, 2e-3), (-5.0, 3.3)])
+def test_uniform_f32_two_roundings(a, b):
+    """The reading of Listing 2: d = b - a, then RN(d u), then RN(a + that), each
+    rounded to float (no fused multiply-add), against exact rational
+    arithmetic with explicit round-to-nearest-even; the fused form differs
+    from it on some of these inputs, so a contraction would fail here."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    w = _f32_words(rng, 3000)
+    r = oracle.transform_words(DIST_UNIFORM, DT_F32, a, b, w.size, w)
+    af, bf = Fraction(float(np.float32(a))), Fraction(float(np.float32(b)))
+    d = Fraction(_round_f32(bf - af))
+    fused_differs = 0
+    for wi, ri in zip(w.tolist(), r.tolist()):
+        u = Fraction(wi >> 8, 2**24)
+        want = _round_f32(af + Fraction(_round_f32(d * u)))
+        if want >= bf:
+            continue  # the clamp case is pinned separately
+        assert ri == want, (wi, ri, want)
+        fused_differs += _round_f32(af + d * u) != want
+    assert fused_differs > 0  # the inputs do tell the two readings apart
+
+
 def test_uniform_f32_exact_cases():
     k = np.arange(0, 1 << 24, 97, dtype=np.uint32)
     w = k << 8
