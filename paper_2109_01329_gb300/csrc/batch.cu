@@ -17,8 +17,9 @@
 // offsets back into the engines.
 //
 // A request whose word offset matches its pointer's 16-byte phase maps each
-// 16-byte group to one Philox block; any other phase stages the blocks of a
-// slice of groups in shared memory and assembles the groups from there.
+// 16-byte group to one Philox block; at any other phase a warp computes 32
+// consecutive blocks and exchanges the straddling words by shuffle (no
+// shared memory anywhere).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -43,10 +44,6 @@ constexpr int kThreads = 256;
 //   BatchReq reqs[count] | uint64_t off[count][2] | int32_t tile_req[tiles]
 size_t align256(size_t x) { return (x + 255u) & ~(size_t)255u; }
 
-// Blocks staged per slice of kThreads groups: 1024 words, up to wpu - 1 words
-// of a unit straddling each end, the phase, block rounding.
-constexpr int kSliceBlocks = kThreads + 4;
-
 // Stores the elements of group (first element e0) that lie in [0, n).
 template <int V>
 __device__ __forceinline__ void store_group(char* base, int64_t e0, int64_t n, uint4 o) {
@@ -70,41 +67,6 @@ __device__ __forceinline__ void store_group(char* base, int64_t e0, int64_t n, u
   }
 }
 
-// Output words of the group whose first element e0 lies kPar elements into
-// unit kb, from the staged words of units [k_lo, k_hi] (unit k_lo at word
-// wphase); every slot index is known at compile time, so the group stays in
-// registers.  Units outside [k_lo, k_hi] hold only elements outside [0, n).
-template <int V, int kPar>
-__device__ __forceinline__ uint4 assemble_group(const uint32_t* swords, int64_t kb, int64_t k_lo,
-                                                int64_t k_hi, uint32_t wphase,
-                                                const TransformParams& t) {
-  using I = VInfo<V>;
-  constexpr int kEpg = 16 / I::es;
-  constexpr int kWpu = I::wpu, kEpu = I::epu, kOwpe = I::ow_per_elem;
-  constexpr int kUnits = (kPar + kEpg - 1) / kEpu + 1;
-  uint32_t gout[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-  for (int j = 0; j < kUnits; ++j) {
-    const int64_t k = kb + j;
-    if (k < k_lo || k > k_hi) continue;
-    const int rel = (int)wphase + (int)(k - k_lo) * kWpu;
-    uint32_t w[kWpu];
-#pragma unroll
-    for (int q = 0; q < kWpu; ++q) w[q] = swords[rel + q];
-    uint32_t o[kWpu];
-    unit_outputs<V>(w, o, t);
-#pragma unroll
-    for (int sl = 0; sl < kEpu; ++sl) {
-      const int slot = j * kEpu + sl - kPar;
-      if (slot >= 0 && slot < kEpg) {
-#pragma unroll
-        for (int q = 0; q < kOwpe; ++q) gout[slot * kOwpe + q] = o[sl * kOwpe + q];
-      }
-    }
-  }
-  return make_uint4(gout[0], gout[1], gout[2], gout[3]);
-}
-
 // The groups [g0, g0 + kThreads ipt) of one request (the whole CTA works on
 // one tile, so every branch below is uniform across it).  Group 0 starts
 // head elements (pw = head es / 4 words) before the output.  When pw is a
@@ -112,12 +74,11 @@ __device__ __forceinline__ uint4 assemble_group(const uint32_t* swords, int64_t 
 // exactly Philox block (off - pw)/4 + g when off - pw is a multiple of 4,
 // else the tail of one block and the head of the next, exchanged between
 // neighbouring lanes.  Otherwise (a Box-Muller pair split by the output's
-// start) each slice of kThreads groups stages the blocks its words span in
-// shared memory (about one block per thread) and each thread assembles its
-// group from there.
+// start) lanes transform pair-aligned virtual groups one element earlier and
+// exchange the straddling element by shuffle.
 template <int V>
 __device__ __forceinline__ void batch_tile(const BatchReq& r, uint64_t off_lo, uint64_t off_hi,
-                                           int64_t g0, int ipt, uint4* sblocks) {
+                                           int64_t g0, int ipt) {
   using I = VInfo<V>;
   constexpr int kEpg = 16 / I::es;
   constexpr int kWpu = I::wpu, kEpu = I::epu;
@@ -172,41 +133,46 @@ __device__ __forceinline__ void batch_tile(const BatchReq& r, uint64_t off_lo, u
     }
     return;
   }
-  const uint32_t* swords = reinterpret_cast<const uint32_t*>(sblocks);
-  for (int i = 0; i < ipt; ++i) {
-    const int64_t gs = g0 + (int64_t)i * kThreads;  // first group of the slice
-    if (gs >= groups) break;
-    // elements of the slice clipped to [0, n), their units and words
-    const int64_t te0 = gs * kEpg - head;
-    const int64_t lo_e = te0 < 0 ? 0 : te0;
-    const int64_t hi_e = (te0 + kThreads * kEpg) < n ? (te0 + kThreads * kEpg) : n;
-    const int64_t k_lo = lo_e / kEpu, k_hi = (hi_e - 1) / kEpu;
-    const uint64_t w_lo = off_lo + (uint64_t)(k_lo * kWpu);
-    const uint64_t w_hi = off_hi + ((w_lo < off_lo) ? 1u : 0u);
-    const uint32_t wphase = (uint32_t)(w_lo & 3u);
-    const uint64_t b_lo = (w_lo >> 2) | (w_hi << 62), b_hi = w_hi >> 2;
-    const int nblocks = (int)((wphase + (k_hi - k_lo + 1) * kWpu + 3) >> 2);  // <= kSliceBlocks
-    for (int j = threadIdx.x; j < nblocks; j += kThreads) {
-      const uint64_t c_lo = b_lo + (uint64_t)j;
+  if constexpr (kEpu == 2) {
+    // A Box-Muller pair split by the output's start (odd head): virtual group
+    // g starts one element before output group g, on a pair boundary, at
+    // word off - pw - es / 4 + 4 g.  Each lane transforms its virtual group
+    // (words from its block and, at a non-zero phase, the next lane's) and
+    // output group g is virtual group g without its first element plus the
+    // first element of virtual group g + 1, taken from lane + 1: 30 groups
+    // per warp, every pair transformed once, no shared memory.
+    constexpr uint32_t kPv = (uint32_t)(I::es / 4);
+    const uint64_t a_lo = off_lo - (pw + kPv);
+    const uint64_t a_hi = off_hi - ((off_lo < (uint64_t)(pw + kPv)) ? 1u : 0u);
+    const uint64_t b_lo = (a_lo >> 2) | (a_hi << 62), b_hi = a_hi >> 2;
+    const uint32_t ph = (uint32_t)a_lo & 3u;
+    const int lane = threadIdx.x & 31;
+    const int64_t g_end = (g0 + (int64_t)kThreads * ipt) < groups ? (g0 + (int64_t)kThreads * ipt)
+                                                                   : groups;
+    constexpr int kPerWarp = 30;
+    for (int64_t gs = g0 + (int64_t)(threadIdx.x >> 5) * kPerWarp; gs < g_end;
+         gs += (int64_t)kPerWarp * (kThreads / 32)) {
+      const int64_t g = gs + lane;
+      const uint64_t c_lo = b_lo + (uint64_t)g;
       const uint64_t c_hi = b_hi + ((c_lo < b_lo) ? 1u : 0u);
-      sblocks[j] = philox4x32_10(ctr_from(c_lo, c_hi), k0, k1);
-    }
-    __syncthreads();
-    const int64_t e0 = te0 + (int64_t)threadIdx.x * kEpg;
-    if (e0 + kEpg > 0 && e0 < n) {
-      uint4 o;
-      if constexpr (kEpu == 1) {
-        o = assemble_group<V, 0>(swords, e0, k_lo, k_hi, wphase, t);
-      } else {
-        // the parity of e0 is the same for every thread (kEpg is even)
-        const int par = (int)(e0 & 1);
-        const int64_t kb = (e0 - par) >> 1;
-        o = par ? assemble_group<V, 1>(swords, kb, k_lo, k_hi, wphase, t)
-                : assemble_group<V, 0>(swords, kb, k_lo, k_hi, wphase, t);
+      const uint4 b = philox4x32_10(ctr_from(c_lo, c_hi), k0, k1);
+      const uint32_t n0 = __shfl_down_sync(0xFFFFFFFFu, b.x, 1);
+      const uint32_t n1 = __shfl_down_sync(0xFFFFFFFFu, b.y, 1);
+      const uint32_t n2 = __shfl_down_sync(0xFFFFFFFFu, b.z, 1);
+      uint4 w = b;
+      if (ph == 1) {
+        w = make_uint4(b.y, b.z, b.w, n0);
+      } else if (ph == 2) {
+        w = make_uint4(b.z, b.w, n0, n1);
+      } else if (ph == 3) {
+        w = make_uint4(b.w, n0, n1, n2);
       }
-      store_group<V>(base, e0, n, o);
+      const uint4 v = block_outputs<V>(w, t);
+      const uint32_t m0 = __shfl_down_sync(0xFFFFFFFFu, v.x, 1);
+      const uint32_t m1 = __shfl_down_sync(0xFFFFFFFFu, v.y, 1);
+      const uint4 o = I::es == 4 ? make_uint4(v.y, v.z, v.w, m0) : make_uint4(v.z, v.w, m0, m1);
+      if (lane < kPerWarp && g < g_end) store_group<V>(base, g * kEpg - head, n, o);
     }
-    __syncthreads();
   }
 }
 
@@ -214,28 +180,27 @@ __global__ void __launch_bounds__(kThreads) batch_fill_kernel(const BatchReq* __
                                                               const uint64_t* __restrict__ off,
                                                               const int32_t* __restrict__ tile_req,
                                                               int64_t tiles, int ipt) {
-  __shared__ uint4 sblocks[kSliceBlocks];
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int32_t ri = tile_req[t];
     const BatchReq& r = reqs[ri];
     const uint64_t off_lo = off[2 * ri], off_hi = off[2 * ri + 1];
     const int64_t g0 = (t - r.first_tile) * (int64_t)kThreads * ipt;
     switch (r.variant) {  // uniform per tile
-      case V_BITS: batch_tile<V_BITS>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_U01_F32: batch_tile<V_U01_F32>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_UNI_F32: batch_tile<V_UNI_F32>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_U01_F64: batch_tile<V_U01_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_AFF_F64: batch_tile<V_AFF_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_UNI_F64: batch_tile<V_UNI_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_GAUSS_F32: batch_tile<V_GAUSS_F32>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_LOGN_F32: batch_tile<V_LOGN_F32>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_GAUSS_F64: batch_tile<V_GAUSS_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_LOGN_F64: batch_tile<V_LOGN_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_ICDF_GAUSS_F32: batch_tile<V_ICDF_GAUSS_F32>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_ICDF_LOGN_F32: batch_tile<V_ICDF_LOGN_F32>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_ICDF_GAUSS_F64: batch_tile<V_ICDF_GAUSS_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      case V_STDGAUSS_F64: batch_tile<V_STDGAUSS_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
-      default: batch_tile<V_ICDF_LOGN_F64>(r, off_lo, off_hi, g0, ipt, sblocks); break;
+      case V_BITS: batch_tile<V_BITS>(r, off_lo, off_hi, g0, ipt); break;
+      case V_U01_F32: batch_tile<V_U01_F32>(r, off_lo, off_hi, g0, ipt); break;
+      case V_UNI_F32: batch_tile<V_UNI_F32>(r, off_lo, off_hi, g0, ipt); break;
+      case V_U01_F64: batch_tile<V_U01_F64>(r, off_lo, off_hi, g0, ipt); break;
+      case V_AFF_F64: batch_tile<V_AFF_F64>(r, off_lo, off_hi, g0, ipt); break;
+      case V_UNI_F64: batch_tile<V_UNI_F64>(r, off_lo, off_hi, g0, ipt); break;
+      case V_GAUSS_F32: batch_tile<V_GAUSS_F32>(r, off_lo, off_hi, g0, ipt); break;
+      case V_LOGN_F32: batch_tile<V_LOGN_F32>(r, off_lo, off_hi, g0, ipt); break;
+      case V_GAUSS_F64: batch_tile<V_GAUSS_F64>(r, off_lo, off_hi, g0, ipt); break;
+      case V_LOGN_F64: batch_tile<V_LOGN_F64>(r, off_lo, off_hi, g0, ipt); break;
+      case V_ICDF_GAUSS_F32: batch_tile<V_ICDF_GAUSS_F32>(r, off_lo, off_hi, g0, ipt); break;
+      case V_ICDF_LOGN_F32: batch_tile<V_ICDF_LOGN_F32>(r, off_lo, off_hi, g0, ipt); break;
+      case V_ICDF_GAUSS_F64: batch_tile<V_ICDF_GAUSS_F64>(r, off_lo, off_hi, g0, ipt); break;
+      case V_STDGAUSS_F64: batch_tile<V_STDGAUSS_F64>(r, off_lo, off_hi, g0, ipt); break;
+      default: batch_tile<V_ICDF_LOGN_F64>(r, off_lo, off_hi, g0, ipt); break;
     }
   }
 }

@@ -16,6 +16,12 @@
 //      one 128-byte row per instruction with 4-byte stores.
 // Chunks are placed so that every chunk starts on a 16-byte output boundary
 // (the first chunk of a stream has virtual head units), hence aligned rows.
+// When the output's start splits a Box-Muller pair (an odd element offset
+// into a 16-byte group) each chunk starts one pair earlier, with the pair
+// that straddles its first 16-byte boundary, and stages its outputs shifted
+// by one element (a one-element carry from pair to pair), so the rows are
+// again whole 16-byte groups; the straddling pair is computed by both
+// neighbouring chunks.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -57,19 +63,24 @@ struct MrgParams {
   uint32_t stream_tab[kJumpLevels][2][9];  // A^(stride 2^k)
 };
 
-// p mod m for the products of one step (p < 2^54): one 64-bit fold of
-// 2^32 = c (mod m), then 32-bit folds of the small remaining carry, then one
-// conditional subtraction.
+// p mod m for the products of one step (p < 2^54), folding 2^32 = c (mod m)
+// with as few 32x32 -> 64-bit products as the ranges allow (they take twice
+// the multiplier's time of a 32-bit product): m1: the high word times c1 fits
+// 32 bits, so one 32-bit product, an add whose carry out is worth c1, and a
+// conditional subtraction; m2: one wide fold (the high word times c2 needs
+// 37 bits), then the same 32-bit step.
 __device__ __forceinline__ uint32_t red_m1(uint64_t p) {
-  const uint64_t t = (uint64_t)(uint32_t)p + (p >> 32) * (uint64_t)mrg::C1;  // < 2^32 + 2^30
-  const uint32_t u = (uint32_t)t + (uint32_t)(t >> 32) * mrg::C1;          // < 2^32
+  const uint32_t lo = (uint32_t)p;
+  const uint32_t u0 = lo + (uint32_t)(p >> 32) * mrg::C1;  // high word < 2^22: product < 2^30
+  const uint32_t u = u0 + (u0 < lo ? mrg::C1 : 0u);        // a carry out of 2^32 is worth c1
   return u >= mrg::M1 ? u - mrg::M1 : u;
 }
 __device__ __forceinline__ uint32_t red_m2(uint64_t p) {
   const uint64_t t = (uint64_t)(uint32_t)p + (p >> 32) * (uint64_t)mrg::C2;  // < 2^32 + 2^37
-  const uint64_t u = (uint64_t)(uint32_t)t + (t >> 32) * (uint64_t)mrg::C2;  // < 2^32 + 2^20
-  const uint32_t v = (uint32_t)u + (uint32_t)(u >> 32) * mrg::C2;          // < 2^32
-  return v >= mrg::M2 ? v - mrg::M2 : v;
+  const uint32_t tl = (uint32_t)t;
+  const uint32_t u0 = tl + (uint32_t)(t >> 32) * mrg::C2;  // t >> 32 < 2^6: product < 2^21
+  const uint32_t u = u0 + (u0 < tl ? mrg::C2 : 0u);
+  return u >= mrg::M2 ? u - mrg::M2 : u;
 }
 
 struct MrgRegs {
@@ -161,9 +172,34 @@ __device__ __forceinline__ void gen_unit(MrgRegs& st, uint32_t* o, const Transfo
   unit_outputs<V>(w, o, t);
 }
 
-template <int V, bool kAligned>
+// kMode: 0 output not 16-byte alignable (row-by-row 4-byte copy-out);
+// 1 chunks start on 16-byte boundaries at unit boundaries; 2 chunks start on
+// 16-byte boundaries one element into a Box-Muller pair (carry mode).
+// The 16-byte stage chunk from 4 new output words: as they are, or (carry
+// mode) shifted up by one element of kOwpe words behind the carried element,
+// whose place the new last element takes.
+template <bool kCarry, int kOwpe>
+__device__ __forceinline__ uint4 shift_in(uint32_t* carry, const uint32_t* o4) {
+  if constexpr (!kCarry) {
+    return make_uint4(o4[0], o4[1], o4[2], o4[3]);
+  } else if constexpr (kOwpe == 1) {
+    const uint4 v = make_uint4(carry[0], o4[0], o4[1], o4[2]);
+    carry[0] = o4[3];
+    return v;
+  } else {
+    const uint4 v = make_uint4(carry[0], carry[1], o4[0], o4[1]);
+    carry[0] = o4[2];
+    carry[1] = o4[3];
+    return v;
+  }
+}
+
+template <int V, int kMode>
 __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
+  constexpr bool kAligned = kMode != 0;
+  constexpr bool kCarry = kMode == 2;
   constexpr int kWpu = VInfo<V>::wpu;
+  constexpr int kOwpe = VInfo<V>::ow_per_elem;
   constexpr int kSu = kRowWords / kWpu;  // units per sub-chunk
   // per warp: 32 rows (one per lane) of 8 16-byte chunks; chunk q of row r is
   // kept at position q ^ (r & 7), so a lane's chunk stores and the copy-out's
@@ -206,6 +242,18 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
     jump(st, e_lo, e_hi);
   }
 
+  // carry mode: the chunk's first unit straddles its first 16-byte boundary;
+  // only its second element is output here (the previous chunk outputs the
+  // first), and every later element moves up one place
+  uint32_t carry[kCarry ? kOwpe : 1];
+  if constexpr (kCarry) {
+    uint32_t o[kWpu];
+#pragma unroll
+    for (int i = 0; i < kWpu; ++i) o[i] = 0u;
+    if (active && u_first >= 0 && u_first < p.units) gen_unit<V>(st, o, p.t);
+#pragma unroll
+    for (int i = 0; i < kOwpe; ++i) carry[i] = o[kOwpe + i];
+  }
   const int64_t nsub = p.chunk_units / kSu;
   uint32_t* out_words = reinterpret_cast<uint32_t*>(p.out);
   // Aligned copy-out: lane copies 16-byte piece (lane & 7) of rows
@@ -220,11 +268,12 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
                                  : p.total_chunks;
   const int rows_active = (int)((lim_chunks - cw) < 32 ? (lim_chunks - cw) : 32);
   const int64_t row_stride = 4 * p.chunk_units * kWpu;  // words between rows it and it + 1
-  const int64_t ow_lane =
-      ((cw_in + (lane >> 3)) * p.chunk_units - p.head_units) * kWpu + (lane & 7) * 4;
+  const int64_t ow_lane = ((cw_in + (lane >> 3)) * p.chunk_units - p.head_units) * kWpu +
+                          (kCarry ? kOwpe : 0) + (lane & 7) * 4;
   uint32_t* stream_out = out_words + sw * p.out_words;
   for (int64_t q = 0; q < nsub; ++q) {
-    const int64_t ub = u_first + q * kSu;  // first unit of this sub-chunk
+    // first unit of this sub-chunk (in carry mode after the straddling one)
+    const int64_t ub = u_first + (kCarry ? 1 : 0) + q * kSu;
     constexpr int kUpc = 4 / kWpu;          // units per 16-byte chunk
     if (active) {
       if (ub >= 0 && ub + kSu <= p.units) {
@@ -234,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
           uint32_t o4[4];
 #pragma unroll
           for (int u = 0; u < kUpc; ++u) gen_unit<V>(st, o4 + u * kWpu, p.t);
-          stage[warp][lane][ch ^ (lane & 7)] = make_uint4(o4[0], o4[1], o4[2], o4[3]);
+          stage[warp][lane][ch ^ (lane & 7)] = shift_in<kCarry, kOwpe>(carry, o4);
         }
       } else {
         for (int ch = 0; ch < 8; ++ch) {
@@ -244,7 +293,7 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
             const int64_t unit = ub + ch * kUpc + u;
             if (unit >= 0 && unit < p.units) gen_unit<V>(st, o4 + u * kWpu, p.t);
           }
-          stage[warp][lane][ch ^ (lane & 7)] = make_uint4(o4[0], o4[1], o4[2], o4[3]);
+          stage[warp][lane][ch ^ (lane & 7)] = shift_in<kCarry, kOwpe>(carry, o4);
         }
       }
     }
@@ -365,9 +414,12 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
   const uintptr_t addr = (uintptr_t)r.out;
   const uint32_t phase_w = (uint32_t)((addr & 15u) / 4u);
   const uint64_t stream_bytes = (uint64_t)r.n * I::es;
-  const bool aligned = (r.num_streams == 1 || (stream_bytes % 16u) == 0) &&
-                       (phase_w % (uint32_t)I::wpu) == 0;
-  p.head_units = aligned ? (int64_t)(phase_w / I::wpu) : 0;
+  const bool uniform_streams = r.num_streams == 1 || (stream_bytes % 16u) == 0;
+  const bool aligned = uniform_streams && (phase_w % (uint32_t)I::wpu) == 0;
+  // a Box-Muller pair split by the output's start: head elements odd
+  const int64_t head_e = (int64_t)(phase_w * 4u / I::es);
+  const bool carry = uniform_streams && !aligned && I::epu == 2 && (head_e & 1) != 0;
+  p.head_units = aligned ? (int64_t)(phase_w / I::wpu) : carry ? (head_e + 1) / 2 : 0;
 
   // About one resident wave of threads, one chunk each (2048 threads per SM,
   // or the tuned count).
@@ -438,9 +490,11 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     return GRNG_ERR_UNSUPPORTED;
   }
   if (aligned) {
-    mrg_fill_kernel<V, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+    mrg_fill_kernel<V, 1><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+  } else if (carry) {
+    if constexpr (I::epu == 2) mrg_fill_kernel<V, 2><<<(unsigned)grid, kThreads, 0, stream>>>(p);
   } else {
-    mrg_fill_kernel<V, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+    mrg_fill_kernel<V, 0><<<(unsigned)grid, kThreads, 0, stream>>>(p);
   }
   const cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) {

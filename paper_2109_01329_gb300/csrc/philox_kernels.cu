@@ -18,9 +18,9 @@
 //     neighbouring lanes by shuffle.  When the output's start splits a
 //     Box-Muller pair, lanes transform pair-aligned groups one element
 //     earlier and exchange the straddling element too (30 groups per warp).
-//   * staged kernel: substreams at another phase.  A CTA computes the blocks
-//     covering a tile of 256 groups into shared memory, then each thread
-//     assembles its group from the words it needs.
+//   * multi-shift kernel: substreams at another phase or alignment, the
+//     shift kernel's exchange applied per stream (a warp works on 30 groups
+//     of one stream).
 // Both write every output exactly once; results do not depend on the launch
 // geometry (each output is a function of its word index only).
 #include <cuda_runtime.h>
@@ -286,96 +286,87 @@ __global__ void __launch_bounds__(kThreads) philox_multi_kernel(const __grid_con
   }
 }
 
-struct StagedParams {
+// Substreams at any word phase and pointer alignment: stream s writes
+// out + s n elements from word offset off + s stride, and its 16-byte groups
+// are found as in the shift kernel, per stream.  A warp takes one chunk of
+// 30 groups of one stream, so the stream's phase, head and pair split are
+// uniform across the warp: lanes compute 32 consecutive blocks, take the
+// next block's first words from lane + 1, and, when the stream's start
+// splits a Box-Muller pair, transform pair-aligned virtual groups one
+// element earlier and exchange the straddling element (as kSplit above).
+struct MultiShiftParams {
   TransformParams t;
-  void* out;
+  char* out;                 // element 0 of stream 0
   int64_t n;                 // elements per stream
-  int64_t num_streams;
-  int64_t tiles_per_stream;  // tiles of kThreads groups
+  int64_t cps;               // warp chunks per stream
+  int64_t total;             // cps * num_streams
   uint64_t off_lo, off_hi;   // word offset of stream 0
   uint64_t stride_lo, stride_hi;
   PhiloxRoundKeys rk;
 };
 
-// Blocks per tile: 256 groups are 1024 words, plus up to 3 words of a unit
-// straddling each end, plus block rounding.
-constexpr int kTileBlocks = kThreads + 4;
+constexpr int kMultiShiftPer = 30;
 
 template <int V>
-__global__ void __launch_bounds__(kThreads) philox_staged_kernel(const __grid_constant__ StagedParams p) {
+__global__ void __launch_bounds__(kThreads) philox_multishift_kernel(
+    const __grid_constant__ MultiShiftParams p) {
   using I = VInfo<V>;
   constexpr int kEpg = 16 / I::es;
-  constexpr int kWpu = I::wpu;
-  constexpr int kEpu = I::epu;
-  constexpr int kOwpe = I::ow_per_elem;
-  __shared__ uint4 sblocks[kTileBlocks];
-  const uint32_t* swords = reinterpret_cast<const uint32_t*>(sblocks);
-
-  const int64_t total_tiles = p.num_streams * p.tiles_per_stream;
-  for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-    const int64_t s = tile / p.tiles_per_stream;
-    const int64_t q = tile - s * p.tiles_per_stream;
-    char* sbase = reinterpret_cast<char*>(p.out) + (s * p.n) * I::es;
-    const int64_t head = (int64_t)(((uintptr_t)sbase & 15u) / I::es);
-    // elements of this tile, clipped to [0, n)
-    const int64_t te0 = q * kThreads * kEpg - head;
-    const int64_t lo_e = te0 < 0 ? 0 : te0;
-    const int64_t hi_e = (te0 + kThreads * kEpg) < p.n ? (te0 + kThreads * kEpg) : p.n;
-    if (lo_e >= hi_e) continue;  // uniform across the CTA
-    const int64_t k_lo = lo_e / kEpu;
-    const int64_t k_hi = (hi_e - 1) / kEpu;
-    // first word of unit k_lo: W = off + s * stride + k_lo * wpu (128-bit)
-    uint64_t w_lo = p.off_lo, w_hi = p.off_hi;
+  constexpr uint32_t kWpe = (uint32_t)(I::es / 4);  // words per element
+  const int lane = threadIdx.x & 31;
+  const int64_t TW = (int64_t)gridDim.x * (kThreads / 32);
+  // the loop bound depends only on the warp: every shuffle has all 32 lanes
+  for (int64_t c = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); c < p.total;
+       c += TW) {
+    const int64_t s = c / p.cps;
+    const int64_t k = c - s * p.cps;
+    char* sbase = p.out + s * p.n * I::es;
+    const uint32_t head = (uint32_t)(((uintptr_t)sbase & 15u) / (uint32_t)I::es);
+    uint4* gbase = reinterpret_cast<uint4*>((uintptr_t)sbase & ~(uintptr_t)15);
+    const bool split = I::epu == 2 && (head & 1u) != 0;
+    // first word of (virtual) group 0: off + s stride - head es/4 (one
+    // element earlier when split), 128-bit
+    uint64_t a_lo = p.off_lo, a_hi = p.off_hi;
     {
       const uint64_t us = (uint64_t)s;
-      add128(w_lo, w_hi, us * p.stride_lo, __umul64hi(us, p.stride_lo) + us * p.stride_hi);
-      add128(w_lo, w_hi, (uint64_t)(k_lo * kWpu), 0);
+      add128(a_lo, a_hi, us * p.stride_lo, __umul64hi(us, p.stride_lo) + us * p.stride_hi);
+      const uint64_t back = (uint64_t)(head * kWpe + (split ? kWpe : 0u));
+      a_hi -= (a_lo < back) ? 1u : 0u;
+      a_lo -= back;
     }
-    const uint32_t wphase = (uint32_t)(w_lo & 3u);
-    // block counter of the first word
-    const uint64_t b_lo = (w_lo >> 2) | (w_hi << 62);
-    const uint64_t b_hi = w_hi >> 2;
-    const int64_t nwords = (k_hi - k_lo + 1) * kWpu;
-    const int nblocks = (int)((wphase + nwords + 3) >> 2);
-    for (int i = threadIdx.x; i < nblocks; i += kThreads) {
-      uint64_t c_lo = b_lo, c_hi = b_hi;
-      add128(c_lo, c_hi, (uint64_t)i, 0);
-      sblocks[i] = philox4x32_10(ctr_from(c_lo, c_hi), p.rk);
+    const uint64_t b_lo = (a_lo >> 2) | (a_hi << 62), b_hi = a_hi >> 2;
+    const uint32_t ph = (uint32_t)a_lo & 3u;
+    const int64_t groups = ((int64_t)head + p.n + kEpg - 1) / kEpg;
+    const int64_t j = k * kMultiShiftPer + lane;
+    const uint64_t c_lo = b_lo + (uint64_t)j;
+    const uint64_t c_hi = b_hi + ((c_lo < b_lo) ? 1u : 0u);
+    const uint4 b = philox4x32_10(ctr_from(c_lo, c_hi), p.rk);
+    const uint32_t n0 = __shfl_down_sync(0xFFFFFFFFu, b.x, 1);
+    const uint32_t n1 = __shfl_down_sync(0xFFFFFFFFu, b.y, 1);
+    const uint32_t n2 = __shfl_down_sync(0xFFFFFFFFu, b.z, 1);
+    uint4 w = b;
+    if (ph == 1) {
+      w = make_uint4(b.y, b.z, b.w, n0);
+    } else if (ph == 2) {
+      w = make_uint4(b.z, b.w, n0, n1);
+    } else if (ph == 3) {
+      w = make_uint4(b.w, n0, n1, n2);
     }
-    __syncthreads();
-
-    const int64_t e0 = te0 + (int64_t)threadIdx.x * kEpg;
-    const int64_t ge_lo = e0 < 0 ? 0 : e0;
-    const int64_t ge_hi = (e0 + kEpg) < p.n ? (e0 + kEpg) : p.n;
-    if (ge_lo < ge_hi) {
-      uint32_t gout[4] = {0u, 0u, 0u, 0u};
-      const int64_t ku_lo = ge_lo / kEpu;
-      const int64_t ku_hi = (ge_hi - 1) / kEpu;
-      for (int64_t k = ku_lo; k <= ku_hi; ++k) {
-        const int64_t rel = (int64_t)wphase + (k - k_lo) * kWpu;
-        uint32_t w[kWpu];
-#pragma unroll
-        for (int i = 0; i < kWpu; ++i) w[i] = swords[rel + i];
-        uint32_t o[kWpu];
-        unit_outputs<V>(w, o, p.t);
-#pragma unroll
-        for (int sl = 0; sl < kEpu; ++sl) {
-          const int64_t e = k * kEpu + sl;
-          if (e >= e0 && e < e0 + kEpg) {
-            const int pos = (int)(e - e0) * kOwpe;
-#pragma unroll
-            for (int i = 0; i < kOwpe; ++i) gout[pos + i] = o[sl * kOwpe + i];
-          }
-        }
-      }
-      const uint4 ov = make_uint4(gout[0], gout[1], gout[2], gout[3]);
-      if (ge_lo == e0 && ge_hi == e0 + kEpg) {
-        store16(sbase + e0 * I::es, ov);
+    const uint4 v = block_outputs<V>(w, p.t);
+    uint4 o = v;
+    if constexpr (I::epu == 2) {
+      const uint32_t m0 = __shfl_down_sync(0xFFFFFFFFu, v.x, 1);
+      const uint32_t m1 = __shfl_down_sync(0xFFFFFFFFu, v.y, 1);
+      if (split) o = I::es == 4 ? make_uint4(v.y, v.z, v.w, m0) : make_uint4(v.z, v.w, m0, m1);
+    }
+    if (lane < kMultiShiftPer && j < groups) {
+      const int64_t e0 = j * kEpg - (int64_t)head;
+      if (e0 >= 0 && e0 + kEpg <= p.n) {
+        gbase[j] = o;
       } else {
-        store_partial<V>(sbase, e0, p.n, ov);
+        store_partial<V>(sbase, e0, p.n, o);
       }
     }
-    __syncthreads();
   }
 }
 
@@ -556,14 +547,15 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
       launch_shift<V, true>(p, a_lo, a_hi, sms, geom, stream);
     }
   } else {
-    StagedParams p;
+    // substreams at any other phase or alignment
+    MultiShiftParams p;
     p.t = r.t;
-    p.out = r.out;
+    p.out = reinterpret_cast<char*>(r.out);
     p.n = r.n;
-    p.num_streams = r.num_streams;
-    // at most 16 / es - 1 head elements per stream
+    // groups of a stream with the largest head (16 / es - 1 elements)
     const int64_t max_groups = (r.n + (kEpg - 1) + kEpg - 1) / kEpg;
-    p.tiles_per_stream = (max_groups + kThreads - 1) / kThreads;
+    p.cps = (max_groups + kMultiShiftPer - 1) / kMultiShiftPer;
+    p.total = p.cps * r.num_streams;
     p.off_lo = r.off_lo;
     p.off_hi = r.off_hi;
     p.stride_lo = r.stride_lo;
@@ -572,13 +564,14 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     static std::atomic<int> occ_cache{0};
     int occ = occ_cache.load(std::memory_order_relaxed);
     if (occ == 0) {
-      occ = blocks_per_sm(philox_staged_kernel<V>);
+      occ = blocks_per_sm(philox_multishift_kernel<V>);
       occ_cache.store(occ, std::memory_order_relaxed);
     }
-    int64_t grid = p.num_streams * p.tiles_per_stream;
+    int64_t grid = (p.total + (kThreads / 32) - 1) / (kThreads / 32);
     const int64_t cap = (int64_t)sms * ctas_cap(occ, geom);
     if (grid > cap) grid = cap;
-    philox_staged_kernel<V><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+    if (grid < 1) grid = 1;
+    philox_multishift_kernel<V><<<(unsigned)grid, kThreads, 0, stream>>>(p);
   }
   const cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) {
