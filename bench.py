@@ -198,23 +198,20 @@ def oracle_rate(seconds_per_case: float, cores: int, n_cap: int):
     return rates, detail
 
 
-# 32x32 -> 64-bit products per output sample, counted from the algorithms as
+# 32x32 products per output sample, counted from the algorithms as
 # implemented: Philox4x32-10 is 20 products per 4-word block; an MRG32k3a word
-# is 9 (per component two multiplier products, then the folds of 2^32 = c
-# mod m: one wide fold and one carry fold for m1, two wide folds and one
-# carry fold for m2); the fixed-point FP64 Box-Muller pair is 42 products
-# (log: 12, square root: 6, sine and cosine: 18, the two final products: 6)
-# on top of the products of its 4 words.
+# is 7 (per component two multiplier products, then the folds of 2^32 = c
+# mod m: one 32-bit product for m1, one wide and one 32-bit product for m2);
+# the fixed-point FP64 Box-Muller pair is 42 products (log: 12, square root:
+# 6, sine and cosine: 18, the two final products: 6) on top of the products
+# of its 4 words.
 BM64_PRODUCTS_PER_PAIR = 42
 
 # DRAM bytes (read + write) per launch at n = 10^9 from ncu captures of the
 # current kernels: one launch of 2.68e8 samples scaled by 1e9 / 2.68e8;
 # a kernel whose code changed after its capture is left out (no number
 # rather than a stale one).
-NCU_TRAFFIC_PER_1E9 = {
-    "mrg32k3a/gaussian_f64": (2.083029e9 + 0.160e6) / 0.268,
-    "philox4x32_10/gaussian_f64": (2.083297e9 + 1.154e6) / 0.268,
-}
+NCU_TRAFFIC_PER_1E9 = {}
 
 # The method's own 32x32 -> 64-bit products per sample, independent of how
 # the kernels implement the arithmetic around them: two multiplier products
@@ -252,9 +249,9 @@ PRODUCTS_PER_SAMPLE = {
     "philox4x32_10/uniform_f64": 10, "philox4x32_10/gaussian_f32": 5,
     "philox4x32_10/gaussian_f64": (20 + BM64_PRODUCTS_PER_PAIR) / 2,
     "philox4x32_10/lognormal_f32": 5,
-    "mrg32k3a/bits_u32": 9, "mrg32k3a/uniform_f32": 9, "mrg32k3a/uniform_f64": 18,
-    "mrg32k3a/gaussian_f32": 9, "mrg32k3a/gaussian_f64": (36 + BM64_PRODUCTS_PER_PAIR) / 2,
-    "mrg32k3a/lognormal_f32": 9,
+    "mrg32k3a/bits_u32": 7, "mrg32k3a/uniform_f32": 7, "mrg32k3a/uniform_f64": 14,
+    "mrg32k3a/gaussian_f32": 7, "mrg32k3a/gaussian_f64": (28 + BM64_PRODUCTS_PER_PAIR) / 2,
+    "mrg32k3a/lognormal_f32": 7,
 }
 
 
