@@ -211,7 +211,10 @@ BM64_PRODUCTS_PER_PAIR = 42
 # current kernels: one launch of 2.68e8 samples scaled by 1e9 / 2.68e8;
 # a kernel whose code changed after its capture is left out (no number
 # rather than a stale one).
-NCU_TRAFFIC_PER_1E9 = {}
+NCU_TRAFFIC_PER_1E9 = {
+    "mrg32k3a/gaussian_f64": (2.082773e9 + 0.145e6) / 0.268,
+    "philox4x32_10/gaussian_f64": (2.083048e9 + 0.280e6) / 0.268,
+}
 
 # The method's own 32x32 -> 64-bit products per sample, independent of how
 # the kernels implement the arithmetic around them: two multiplier products
@@ -356,6 +359,74 @@ def run_config3(grng, torch, dev, stream, hbm_peak, reps=3):
         res[en] = {"ms": round(ms, 3), "gsamples_s": round(ns * per / ms / 1e6, 2),
                    "write_gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4)}
     del out
+    return res
+
+
+def _event_ms(torch, stream, fn, reps):
+    """Median CUDA-event time of fn() on stream after one untimed call."""
+    with torch.cuda.stream(stream):
+        fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
+def run_offset_paths(grng, torch, dev, n, buf, stream, reps=3):
+    """Fills whose output start or word phase does not line up with 16-byte
+    groups, each beside the same fill lined up: a Box-Muller pair split by the
+    pointer (output at element offset 1), substreams of odd length at a word
+    stride that is not a multiple of 4, and the 4096-request batch with every
+    output at element offset 1."""
+    res = {}
+    for ek, en in ENGINES:
+        for name, kind, dtype in (("gaussian_f32", 2, 1), ("gaussian_f64", 2, 2)):
+            es = 8 if dtype == 2 else 4
+            tdt = torch.float32 if dtype == 1 else torch.float64
+            whole = buf[: (n + 2) * es].view(tdt)
+            d = grng.Distribution(kind, dtype, 0.0, 1.0)
+            times = {}
+            for label, out in (("aligned", whole[:n]), ("pointer_plus_1", whole[1:n + 1])):
+                e = grng.Engine(ek, W.SWEEP_SEED, 0)
+                times[label] = _event_ms(torch, stream,
+                                         lambda: grng.generate(d, e, out, stream=stream), reps)
+            res[f"{en}/{name}"] = {k: round(v, 4) for k, v in times.items()}
+            res[f"{en}/{name}"]["ratio"] = round(times["pointer_plus_1"] / times["aligned"], 3)
+    # substreams: 16384 x 65536 FP32 gaussians, stride 2^40, against
+    # 16384 x 65537 at stride 2^40 + 1 (every stream at its own phase)
+    d = grng.Distribution(2, 1, 0.0, 1.0)
+    for ek, en in ENGINES:
+        times = {}
+        for label, per, stride in (("aligned", 65536, 1 << 40), ("odd_len_odd_stride", 65537,
+                                                                  (1 << 40) + 1)):
+            out = buf[: 16384 * per * 4].view(torch.float32)
+            e = grng.Engine(ek, W.SWEEP_SEED, 0)
+            times[label] = _event_ms(torch, stream, lambda: grng.generate_substreams(
+                d, e, out, per, 16384, stride, stream=stream), reps)
+        res[f"{en}/substreams_gaussian_f32"] = {k: round(v, 4) for k, v in times.items()}
+        res[f"{en}/substreams_gaussian_f32"]["ratio"] = round(
+            times["odd_len_odd_stride"] / times["aligned"], 3)
+    # the batched table, outputs at element offset 0 and 1
+    table = W.batched_requests(4096)
+    tdt = {0: torch.int32, 1: torch.float32, 2: torch.float64}
+    times = {}
+    for label, shift in (("aligned", 0), ("pointer_plus_1", 1)):
+        reqs = []
+        for q in table:
+            nm, kind, dtype, p0, p1 = q["dist"]
+            o = torch.empty(q["n"] + shift, dtype=tdt[dtype], device=dev)[shift:]
+            reqs.append((grng.Engine(0, q["seed"], 0), grng.Distribution(kind, dtype, p0, p1), o,
+                         q["n"]))
+        b = grng.Batch(reqs, ipt=8, stream=stream)
+        b.autotune(stream=stream)
+        times[label] = _event_ms(torch, stream, lambda: b.launch(stream=stream), 10)
+        del b, reqs
+    res["batched_4096"] = {k: round(v, 4) for k, v in times.items()}
+    res["batched_4096"]["ratio"] = round(times["pointer_plus_1"] / times["aligned"], 3)
     return res
 
 
@@ -671,7 +742,7 @@ def run_ours(args):
     n = int(args.n)
     hbm_peak, peak_src = _peaks()
     stream = torch.cuda.current_stream(dev)
-    buf = torch.empty(n * 8, dtype=torch.uint8, device=dev)
+    buf = torch.empty(n * 8 + 256, dtype=torch.uint8, device=dev)  # + room for offset outputs
     tdt = {0: torch.int32, 1: torch.float32, 2: torch.float64}
     cases = [(ek, en, d) for ek, en in ENGINES for d in W.SWEEP_DISTS]
     if args.only:
@@ -699,9 +770,13 @@ def run_ours(args):
     for ek, en, (name, kind, dtype, p0, p1) in cases:
         d = grng.Distribution(kind, dtype, p0, p1)
         es = 8 if dtype == 2 else 4
+        gm = {"chosen": None}
         if not args.no_tune:
-            grng.fill_autotune(ek, d, buf[: n * es].view(tdt[dtype]), n, stream=stream)
-        geometry[f"{en}/{name}"] = grng.fill_geometry(ek, d, n)
+            _, t_best, t_builtin = grng.fill_autotune(ek, d, buf[: n * es].view(tdt[dtype]), n,
+                                                      stream=stream)
+            gm = {"tuned_ms": round(t_best, 4), "builtin_ms": round(t_builtin, 4)}
+        gm["chosen"] = grng.fill_geometry(ek, d, n)
+        geometry[f"{en}/{name}"] = gm
     for _ in range(max(args.warmup, 0)):
         one_step()
     torch.cuda.synchronize()
@@ -816,6 +891,7 @@ def run_ours(args):
     # the target statement's headline: Philox FP32 uniform fill at >= 0.80 of
     # its roofline (HBM write bound), against the copy peak and the live
     # write-only probe
+    roofline["target_batched_vs_per_request"] = None  # filled below when the batch runs
     roofline["target_philox_uniform_f32"] = {
         "write_gbs": target["write_gbs"], "frac": target["frac_roofline"],
         "frac_hbm_copy_peak": target["frac_hbm"],
@@ -917,14 +993,20 @@ def run_ours(args):
     if rank == 0 and not args.skip_extra:
         extra = run_extra(grng, torch, dev, n, buf, stream, 3, hbm_peak)
 
-    config1 = config3 = None
+    config1 = config3 = offset_paths = None
     if rank == 0 and not args.skip_configs:
         config1 = run_config1(grng, torch, dev, stream)
         config3 = run_config3(grng, torch, dev, stream, hbm_peak)
+        offset_paths = run_offset_paths(grng, torch, dev, n, buf, stream)
 
     batched = None
     if rank == 0 and not args.skip_batched:
         batched = run_batched(grng, torch, dev, args.batch_reps)
+
+    if batched is not None:
+        roofline["target_batched_vs_per_request"] = {
+            "speedup": batched["speedup"], "batched_graph_ms": batched["batched_graph_ms_p50"],
+            "per_request_ms": batched["per_request_ms_p50"], "meets_5x": batched["speedup"] >= 5}
 
     serving = None
     if rank == 0 and args.serve_seconds > 0:
@@ -958,6 +1040,7 @@ def run_ours(args):
                          "op_rates_per_s": {k: round(v, 1) for k, v in ops.items()}},
             "per_kernel": per_kernel, "curand": curand, "tts": tts, "other_fills": extra,
             "config1_2pow20_uniform": config1, "config3_substreams": config3,
+            "offset_paths": offset_paths,
             "batched": batched, "serving": serving,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": args.steps * len(cases)}

@@ -268,12 +268,14 @@ GRNG_API grng_status grng_generate_host(const grng_distribution* dist, grng_engi
  * memory of n elements, aligned to the element size) at each candidate
  * geometry (Philox: 0, 1, 2, 3, 4, 5, 6, 8; MRG32k3a: 0, 1, 2, 4, 6, 12, 16),
  * with a private engine (no caller engine moves), and keeps the fastest for
- * n's bucket; *best_geometry and *best_ms (either may be NULL) receive it.
- * Synchronises `stream`.  Errors: INVALID_ARG (bad kind, dist, n < 1, NULL
- * dev_buf), CUDA. */
+ * n's bucket (a candidate must beat the earlier best by 1 %, so ties keep the
+ * built-in choice); *best_geometry, *best_ms and *builtin_ms (the built-in
+ * choice's time; each may be NULL) receive the result.  Synchronises
+ * `stream`.  Errors: INVALID_ARG (bad kind, dist, n < 1, NULL dev_buf), CUDA. */
 GRNG_API grng_status grng_fill_autotune(int32_t engine_kind, const grng_distribution* dist,
                                         int64_t n, void* dev_buf, grng_stream_t stream,
-                                        int32_t* best_geometry, float* best_ms);
+                                        int32_t* best_geometry, float* best_ms,
+                                        float* builtin_ms);
 
 /* Sets / reads the geometry of n's bucket (0..64; 0 = built-in). */
 GRNG_API grng_status grng_fill_set_geometry(int32_t engine_kind, const grng_distribution* dist,

@@ -152,6 +152,7 @@ def load() -> ctypes.CDLL:
         L.grng_server_set_release_delay.argtypes = [vp, ctypes.c_int64]
         L.grng_fill_autotune.argtypes = [ctypes.c_int32, ctypes.POINTER(_Dist), ctypes.c_int64, vp,
                                          vp, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_float),
                                          ctypes.POINTER(ctypes.c_float)]
         L.grng_fill_set_geometry.argtypes = [ctypes.c_int32, ctypes.POINTER(_Dist),
                                              ctypes.c_int64, ctypes.c_int32]
@@ -450,7 +451,7 @@ def fill_autotune(engine_kind: int, dist: Distribution, buf, n: int | None = Non
                   stream=None):
     """grng_fill_autotune: times the candidate launch geometries of a fill of n
     outputs into the CUDA tensor buf and keeps the fastest for n's size
-    bucket; returns (geometry, ms)."""
+    bucket; returns (geometry, ms, ms of the built-in geometry)."""
     import torch
 
     if not buf.is_cuda or not _torch_dtype_ok(buf, dist.dtype):
@@ -459,14 +460,14 @@ def fill_autotune(engine_kind: int, dist: Distribution, buf, n: int | None = Non
     if n < 1 or n > buf.numel():
         raise ValueError("n outside [1, buf.numel()]")
     d = dist._c()
-    geo, ms = ctypes.c_int32(), ctypes.c_float()
+    geo, ms, ms0 = ctypes.c_int32(), ctypes.c_float(), ctypes.c_float()
     with torch.cuda.device(buf.device):
         _check(load().grng_fill_autotune(engine_kind, ctypes.byref(d), n,
                                          ctypes.c_void_p(buf.data_ptr()),
                                          ctypes.c_void_p(_stream_ptr(buf.device, stream)),
-                                         ctypes.byref(geo), ctypes.byref(ms)),
+                                         ctypes.byref(geo), ctypes.byref(ms), ctypes.byref(ms0)),
                "grng_fill_autotune")
-    return geo.value, ms.value
+    return geo.value, ms.value, ms0.value
 
 
 def fill_geometry(engine_kind: int, dist: Distribution, n: int, geometry: int | None = None) -> int:

@@ -133,7 +133,7 @@ grng_status grng_fill_get_geometry(int32_t engine_kind, const grng_distribution*
 
 grng_status grng_fill_autotune(int32_t engine_kind, const grng_distribution* dist, int64_t n,
                                void* dev_buf, grng_stream_t stream_in, int32_t* best_geometry,
-                               float* best_ms) {
+                               float* best_ms, float* builtin_ms) {
   TransformParams t;
   int v = 0;
   grng_status st = fill_transform_params(dist, &t, &v);
@@ -162,7 +162,7 @@ grng_status grng_fill_autotune(int32_t engine_kind, const grng_distribution* dis
     grng_engine_destroy(e);
     return GRNG_ERR_CUDA;
   }
-  float best = 1e30f;
+  float best = 1e30f, t_builtin = 0.f;
   int32_t arg = before;
   for (int i = 0; i < ncand && st == GRNG_OK; ++i) {
     slot.store(cand[i], std::memory_order_relaxed);
@@ -180,6 +180,7 @@ grng_status grng_fill_autotune(int32_t engine_kind, const grng_distribution* dis
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    if (cand[i] == 0) t_builtin = ms / 3;
     if (ms / 3 < best * 0.99f) {  // ties keep the earlier (the built-in choice first)
       best = ms / 3;
       arg = cand[i];
@@ -192,6 +193,7 @@ grng_status grng_fill_autotune(int32_t engine_kind, const grng_distribution* dis
   if (st != GRNG_OK) return st;
   if (best_geometry) *best_geometry = arg;
   if (best_ms) *best_ms = best;
+  if (builtin_ms) *builtin_ms = t_builtin;
   return GRNG_OK;
 }
 
