@@ -253,9 +253,11 @@ GRNG_API grng_status grng_generate_host(const grng_distribution* dist, grng_engi
 /* ---------------------------------------------------------- fill geometry
  * Launch geometry of grng_generate / grng_generate_substreams, one integer
  * per (engine kind, distribution variant, size bucket = bit length of the
- * element count): Philox4x32-10, the cap on resident CTAs per SM (the kernels
- * loop with a grid stride); MRG32k3a, the threads per SM of the chunk plan in
- * units of 256 (sets the chunk length); 0 = the built-in choice.  Tuning is
+ * element count): Philox4x32-10, the CTAs per SM of its grid-stride kernels
+ * (1..16: a cap on the resident CTAs; 17..64: value - 16 waves of resident
+ * CTAs); MRG32k3a, the threads per SM of the chunk plan in units of 256 (sets
+ * the chunk length); 0 = the built-in choice (Philox: 8 waves of resident
+ * CTAs; MRG32k3a: 2048 threads per SM).  Tuning is
  * what the paper expects of kernels written for the hardware (Sec. 8; Sec. 7
  * shows the launch configuration mattering).  Outputs never depend on the
  * geometry.  The table starts from the file named by the environment
@@ -266,7 +268,8 @@ GRNG_API grng_status grng_generate_host(const grng_distribution* dist, grng_engi
 
 /* Times a fill of n outputs of `dist` into dev_buf (caller-owned device
  * memory of n elements, aligned to the element size) at each candidate
- * geometry (Philox: 0, 1, 2, 3, 4, 5, 6, 8; MRG32k3a: 0, 1, 2, 4, 6, 12, 16),
+ * geometry (Philox: 0, 1, 2, 4, 17, 18, 20, 32, 48, 64; MRG32k3a: 0, 1, 2, 4,
+ * 6, 12, 16),
  * with a private engine (no caller engine moves), and keeps the fastest for
  * n's bucket (a candidate must beat the earlier best by 1 %, so ties keep the
  * built-in choice); *best_geometry, *best_ms and *builtin_ms (the built-in

@@ -172,9 +172,6 @@ __device__ __forceinline__ void gen_unit(MrgRegs& st, uint32_t* o, const Transfo
   unit_outputs<V>(w, o, t);
 }
 
-// kMode: 0 output not 16-byte alignable (row-by-row 4-byte copy-out);
-// 1 chunks start on 16-byte boundaries at unit boundaries; 2 chunks start on
-// 16-byte boundaries one element into a Box-Muller pair (carry mode).
 // The 16-byte stage chunk from 4 new output words: as they are, or (carry
 // mode) shifted up by one element of kOwpe words behind the carried element,
 // whose place the new last element takes.
@@ -194,10 +191,16 @@ __device__ __forceinline__ uint4 shift_in(uint32_t* carry, const uint32_t* o4) {
   }
 }
 
+// kMode: 0 output not 16-byte alignable (row-by-row 4-byte copy-out);
+// 1 chunks start on 16-byte boundaries at unit boundaries; 2 chunks start on
+// 16-byte boundaries one element into a Box-Muller pair (carry mode);
+// 3 substreams of unequal 16-byte phase: each stream has its own head, and
+// its own carry mode when its start splits a pair (a warp's 32 chunks lie in
+// one stream, so both are warp-uniform).
 template <int V, int kMode>
 __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
   constexpr bool kAligned = kMode != 0;
-  constexpr bool kCarry = kMode == 2;
+  constexpr bool kPerStream = kMode == 3;
   constexpr int kWpu = VInfo<V>::wpu;
   constexpr int kOwpe = VInfo<V>::ow_per_elem;
   constexpr int kSu = kRowWords / kWpu;  // units per sub-chunk
@@ -214,7 +217,19 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
     s = cid / p.chunks_per_stream;
     c = cid - s * p.chunks_per_stream;
   }
-  const int64_t u_first = c * p.chunk_units - p.head_units;
+  // the stream's head (virtual units before its output's first 16-byte
+  // group) and whether its start splits a pair
+  int64_t hu = p.head_units;
+  bool kCarry = kMode == 2;
+  if constexpr (kPerStream) {
+    const uint32_t he = (uint32_t)(((uintptr_t)p.out + (uintptr_t)(s * p.n * VInfo<V>::es)) &
+                                   15u) /
+                        (uint32_t)VInfo<V>::es;
+    constexpr uint32_t kEpu = (uint32_t)VInfo<V>::epu;
+    hu = (int64_t)((he + kEpu - 1) / kEpu);
+    kCarry = kEpu == 2 && (he & 1u) != 0;
+  }
+  const int64_t u_first = c * p.chunk_units - hu;
 
   MrgRegs st;
   if (p.chunk_levels > 0) {
@@ -225,6 +240,12 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
     st.b0 = x[3]; st.b1 = x[4]; st.b2 = x[5];
     jump_table(st, p.chunk_tab, p.chunk_levels, active && c > 0 ? (uint64_t)(c - 1) : 0u);
     if (p.stream_levels > 0) jump_table(st, p.stream_tab, p.stream_levels, active ? (uint64_t)s : 0u);
+    if constexpr (kPerStream) {
+      // chunk 1's state is taken at the largest head (p.head_units); a stream
+      // with a smaller head starts its chunks that many units later
+      if (active && c > 0)
+        for (int64_t k = 0; k < (p.head_units - hu) * kWpu; ++k) mrg_next(st);
+    }
   } else {
     st.a0 = p.x[0]; st.a1 = p.x[1]; st.a2 = p.x[2];
     st.b0 = p.x[3]; st.b1 = p.x[4]; st.b2 = p.x[5];
@@ -245,8 +266,8 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
   // carry mode: the chunk's first unit straddles its first 16-byte boundary;
   // only its second element is output here (the previous chunk outputs the
   // first), and every later element moves up one place
-  uint32_t carry[kCarry ? kOwpe : 1];
-  if constexpr (kCarry) {
+  uint32_t carry[kOwpe];
+  if (kCarry) {
     uint32_t o[kWpu];
 #pragma unroll
     for (int i = 0; i < kWpu; ++i) o[i] = 0u;
@@ -268,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
                                  : p.total_chunks;
   const int rows_active = (int)((lim_chunks - cw) < 32 ? (lim_chunks - cw) : 32);
   const int64_t row_stride = 4 * p.chunk_units * kWpu;  // words between rows it and it + 1
-  const int64_t ow_lane = ((cw_in + (lane >> 3)) * p.chunk_units - p.head_units) * kWpu +
+  const int64_t ow_lane = ((cw_in + (lane >> 3)) * p.chunk_units - hu) * kWpu +
                           (kCarry ? kOwpe : 0) + (lane & 7) * 4;
   uint32_t* stream_out = out_words + sw * p.out_words;
   for (int64_t q = 0; q < nsub; ++q) {
@@ -283,7 +304,8 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
           uint32_t o4[4];
 #pragma unroll
           for (int u = 0; u < kUpc; ++u) gen_unit<V>(st, o4 + u * kWpu, p.t);
-          stage[warp][lane][ch ^ (lane & 7)] = shift_in<kCarry, kOwpe>(carry, o4);
+          stage[warp][lane][ch ^ (lane & 7)] = kCarry ? shift_in<true, kOwpe>(carry, o4)
+                                                      : shift_in<false, kOwpe>(carry, o4);
         }
       } else {
         for (int ch = 0; ch < 8; ++ch) {
@@ -293,7 +315,8 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
             const int64_t unit = ub + ch * kUpc + u;
             if (unit >= 0 && unit < p.units) gen_unit<V>(st, o4 + u * kWpu, p.t);
           }
-          stage[warp][lane][ch ^ (lane & 7)] = shift_in<kCarry, kOwpe>(carry, o4);
+          stage[warp][lane][ch ^ (lane & 7)] = kCarry ? shift_in<true, kOwpe>(carry, o4)
+                                                      : shift_in<false, kOwpe>(carry, o4);
         }
       }
     }
@@ -419,7 +442,13 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
   // a Box-Muller pair split by the output's start: head elements odd
   const int64_t head_e = (int64_t)(phase_w * 4u / I::es);
   const bool carry = uniform_streams && !aligned && I::epu == 2 && (head_e & 1) != 0;
-  p.head_units = aligned ? (int64_t)(phase_w / I::wpu) : carry ? (head_e + 1) / 2 : 0;
+  // substreams of unequal phase: per-stream heads up to the largest possible
+  // one, ceil((16 / es - 1) / epu) units
+  const bool per_stream = !uniform_streams;
+  const int64_t hu_max = (16 / I::es - 1 + I::epu - 1) / I::epu;
+  p.head_units = aligned ? (int64_t)(phase_w / I::wpu)
+                 : carry ? (head_e + 1) / 2
+                 : per_stream ? hu_max : 0;
 
   // About one resident wave of threads, one chunk each (2048 threads per SM,
   // or the tuned count).
@@ -493,6 +522,8 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     mrg_fill_kernel<V, 1><<<(unsigned)grid, kThreads, 0, stream>>>(p);
   } else if (carry) {
     if constexpr (I::epu == 2) mrg_fill_kernel<V, 2><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+  } else if (per_stream) {
+    mrg_fill_kernel<V, 3><<<(unsigned)grid, kThreads, 0, stream>>>(p);
   } else {
     mrg_fill_kernel<V, 0><<<(unsigned)grid, kThreads, 0, stream>>>(p);
   }

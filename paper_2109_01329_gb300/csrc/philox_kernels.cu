@@ -169,6 +169,7 @@ struct ShiftParams {
   int64_t n;          // elements
   int64_t head;       // elements of group 0 that lie before out
   int64_t groups;
+  int64_t jf, jl;     // groups [jf, jl) lie wholly inside the output
   int64_t chunks;     // ceil(groups / groups per warp chunk)
   uint64_t base_lo;   // block holding the first word of (virtual) group 0
   uint64_t base_hi;
@@ -181,6 +182,27 @@ __host__ __device__ constexpr int shift_per_warp() {
   return kSplit ? 30 : 31;
 }
 
+// The 4 words of a group whose first word is at phase ph of block b (this
+// lane's), the rest from the next lane's block.
+__device__ __forceinline__ uint4 shift_words(uint4 b, uint32_t ph) {
+  const uint32_t n0 = __shfl_down_sync(0xFFFFFFFFu, b.x, 1);
+  const uint32_t n1 = __shfl_down_sync(0xFFFFFFFFu, b.y, 1);
+  const uint32_t n2 = __shfl_down_sync(0xFFFFFFFFu, b.z, 1);
+  if (ph == 1) return make_uint4(b.y, b.z, b.w, n0);
+  if (ph == 2) return make_uint4(b.z, b.w, n0, n1);
+  if (ph == 3) return make_uint4(b.w, n0, n1, n2);
+  return b;
+}
+
+// Output group from this lane's transformed virtual group v and the next
+// lane's first element (a Box-Muller pair split by the output's start).
+template <int V>
+__device__ __forceinline__ uint4 split_group(uint4 v) {
+  const uint32_t m0 = __shfl_down_sync(0xFFFFFFFFu, v.x, 1);
+  const uint32_t m1 = __shfl_down_sync(0xFFFFFFFFu, v.y, 1);
+  return VInfo<V>::es == 4 ? make_uint4(v.y, v.z, v.w, m0) : make_uint4(v.z, v.w, m0, m1);
+}
+
 template <int V, int U, bool kHiUniform, bool kSplit>
 __device__ __forceinline__ void philox_shift_body(const ShiftParams& p) {
   using I = VInfo<V>;
@@ -188,48 +210,43 @@ __device__ __forceinline__ void philox_shift_body(const ShiftParams& p) {
   constexpr int kPer = shift_per_warp<kSplit>();
   const int lane = threadIdx.x & 31;
   const int64_t TW = (int64_t)gridDim.x * (kThreads / 32);
+  const int64_t c0 = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  // this lane's group of chunk c is j = c kPer + lane; j, the block counter
+  // and the store address advance by increments (dj from chunk c to c + TW)
+  const int64_t dj = TW * kPer;
+  int64_t j = c0 * kPer + lane;
+  uint64_t lo = p.base_lo + (uint64_t)j;
+  uint4* dst = p.gbase + j;
   // the loop bound depends only on the warp: every shuffle has all 32 lanes
-  for (int64_t c = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); c < p.chunks;
-       c += U * TW) {
+  for (int64_t c = c0; c < p.chunks;
+       c += U * TW, j += U * dj, lo += (uint64_t)(U * dj), dst += U * dj) {
     uint4 b[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const uint64_t j = (uint64_t)((c + u * TW) * kPer + lane);
-      const uint64_t lo = p.base_lo + j;
-      const uint64_t hi = kHiUniform ? p.base_hi : p.base_hi + ((lo < p.base_lo) ? 1u : 0u);
-      b[u] = philox4x32_10(ctr_from(lo, hi), p.rk);
+      const uint64_t l = lo + (uint64_t)(u * dj);
+      const uint64_t h = kHiUniform ? p.base_hi : p.base_hi + ((l < p.base_lo) ? 1u : 0u);
+      b[u] = philox4x32_10(ctr_from(l, h), p.rk);
     }
+    // every group of this iteration lies wholly inside the output (uniform)
+    const bool interior = c * kPer >= p.jf && (c + (U - 1) * TW) * kPer + kPer <= p.jl;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      uint4 w = b[u];
-      if (!kSplit || p.ph != 0) {
-        const uint32_t n0 = __shfl_down_sync(0xFFFFFFFFu, b[u].x, 1);
-        const uint32_t n1 = __shfl_down_sync(0xFFFFFFFFu, b[u].y, 1);
-        const uint32_t n2 = __shfl_down_sync(0xFFFFFFFFu, b[u].z, 1);
-        if (p.ph == 1) {
-          w = make_uint4(b[u].y, b[u].z, b[u].w, n0);
-        } else if (p.ph == 2) {
-          w = make_uint4(b[u].z, b[u].w, n0, n1);
-        } else {
-          w = make_uint4(b[u].w, n0, n1, n2);
-        }
-      }
-      const int64_t j = (c + u * TW) * kPer + lane;
-      uint4 o;
-      if constexpr (kSplit) {
-        // every lane transforms its virtual group: lane l + 1's is needed by l
-        const uint4 v = block_outputs<V>(w, p.t);
-        const uint32_t m0 = __shfl_down_sync(0xFFFFFFFFu, v.x, 1);
-        const uint32_t m1 = __shfl_down_sync(0xFFFFFFFFu, v.y, 1);
-        o = I::es == 4 ? make_uint4(v.y, v.z, v.w, m0) : make_uint4(v.z, v.w, m0, m1);
-      }
-      if (lane < kPer && j < p.groups) {
-        if constexpr (!kSplit) o = block_outputs<V>(w, p.t);
-        const int64_t e0 = j * kEpg - p.head;
-        if (e0 >= 0 && e0 + kEpg <= p.n) {
-          p.gbase[j] = o;
-        } else {
-          store_partial<V>(reinterpret_cast<char*>(p.out), e0, p.n, o);
+      const uint4 w = (!kSplit || p.ph != 0) ? shift_words(b[u], p.ph) : b[u];
+      // every lane transforms its (virtual) group; in split mode lane l + 1's
+      // first element is needed by lane l
+      uint4 o = block_outputs<V>(w, p.t);
+      if constexpr (kSplit) o = split_group<V>(o);
+      if (interior) {
+        if (lane < kPer) dst[u * dj] = o;
+      } else {
+        const int64_t ju = j + u * dj;
+        if (lane < kPer && ju < p.groups) {
+          const int64_t e0 = ju * kEpg - p.head;
+          if (e0 >= 0 && e0 + kEpg <= p.n) {
+            dst[u * dj] = o;
+          } else {
+            store_partial<V>(reinterpret_cast<char*>(p.out), e0, p.n, o);
+          }
         }
       }
     }
@@ -307,72 +324,104 @@ struct MultiShiftParams {
 
 constexpr int kMultiShiftPer = 30;
 
+// Where stream s's (virtual) groups start, per stream of a multi-shift fill.
+struct ShiftStream {
+  char* sbase;      // element 0 of the stream
+  uint4* gbase;     // its 16-byte aligned group 0
+  int64_t head;     // elements of group 0 before sbase
+  int64_t groups, jf, jl;
+  uint64_t b_lo, b_hi;  // block of the first word of (virtual) group 0
+  uint32_t ph;
+  bool split;
+};
+
+template <int V>
+__device__ __forceinline__ ShiftStream shift_stream(const MultiShiftParams& p, int64_t s) {
+  using I = VInfo<V>;
+  constexpr int kEpg = 16 / I::es;
+  constexpr uint32_t kWpe = (uint32_t)(I::es / 4);  // words per element
+  ShiftStream t;
+  t.sbase = p.out + s * p.n * I::es;
+  t.head = (int64_t)(((uintptr_t)t.sbase & 15u) / (uint32_t)I::es);
+  t.gbase = reinterpret_cast<uint4*>((uintptr_t)t.sbase & ~(uintptr_t)15);
+  t.split = I::epu == 2 && (t.head & 1) != 0;
+  // first word of (virtual) group 0: off + s stride - head es/4 (one element
+  // earlier when split), 128-bit
+  uint64_t a_lo = p.off_lo, a_hi = p.off_hi;
+  const uint64_t us = (uint64_t)s;
+  add128(a_lo, a_hi, us * p.stride_lo, __umul64hi(us, p.stride_lo) + us * p.stride_hi);
+  const uint64_t back = (uint64_t)t.head * kWpe + (t.split ? kWpe : 0u);
+  a_hi -= (a_lo < back) ? 1u : 0u;
+  a_lo -= back;
+  t.b_lo = (a_lo >> 2) | (a_hi << 62);
+  t.b_hi = a_hi >> 2;
+  t.ph = (uint32_t)a_lo & 3u;
+  t.groups = (t.head + p.n + kEpg - 1) / kEpg;
+  t.jf = t.head > 0 ? 1 : 0;
+  t.jl = ((t.head + p.n) % kEpg) != 0 ? t.groups - 1 : t.groups;
+  return t;
+}
+
 template <int V>
 __global__ void __launch_bounds__(kThreads) philox_multishift_kernel(
     const __grid_constant__ MultiShiftParams p) {
   using I = VInfo<V>;
   constexpr int kEpg = 16 / I::es;
-  constexpr uint32_t kWpe = (uint32_t)(I::es / 4);  // words per element
+  constexpr int kPer = kMultiShiftPer;
   const int lane = threadIdx.x & 31;
-  const int64_t TW = (int64_t)gridDim.x * (kThreads / 32);
-  // the loop bound depends only on the warp: every shuffle has all 32 lanes
-  for (int64_t c = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); c < p.total;
-       c += TW) {
-    const int64_t s = c / p.cps;
-    const int64_t k = c - s * p.cps;
-    char* sbase = p.out + s * p.n * I::es;
-    const uint32_t head = (uint32_t)(((uintptr_t)sbase & 15u) / (uint32_t)I::es);
-    uint4* gbase = reinterpret_cast<uint4*>((uintptr_t)sbase & ~(uintptr_t)15);
-    const bool split = I::epu == 2 && (head & 1u) != 0;
-    // first word of (virtual) group 0: off + s stride - head es/4 (one
-    // element earlier when split), 128-bit
-    uint64_t a_lo = p.off_lo, a_hi = p.off_hi;
-    {
-      const uint64_t us = (uint64_t)s;
-      add128(a_lo, a_hi, us * p.stride_lo, __umul64hi(us, p.stride_lo) + us * p.stride_hi);
-      const uint64_t back = (uint64_t)(head * kWpe + (split ? kWpe : 0u));
-      a_hi -= (a_lo < back) ? 1u : 0u;
-      a_lo -= back;
-    }
-    const uint64_t b_lo = (a_lo >> 2) | (a_hi << 62), b_hi = a_hi >> 2;
-    const uint32_t ph = (uint32_t)a_lo & 3u;
-    const int64_t groups = ((int64_t)head + p.n + kEpg - 1) / kEpg;
-    const int64_t j = k * kMultiShiftPer + lane;
-    const uint64_t c_lo = b_lo + (uint64_t)j;
-    const uint64_t c_hi = b_hi + ((c_lo < b_lo) ? 1u : 0u);
+  // each warp takes a run of consecutive chunks (chunk c = stream c / cps,
+  // chunk c mod cps of it), so a stream's set-up is redone only when the run
+  // enters the next stream; the loop bound depends only on the warp
+  const int64_t W = (int64_t)gridDim.x * (kThreads / 32);
+  const int64_t w = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  const int64_t L = (p.total + W - 1) / W;
+  int64_t c = w * L;
+  const int64_t c_end = (c + L) < p.total ? (c + L) : p.total;
+  if (c >= c_end) return;
+  int64_t s = c / p.cps;
+  int64_t k = c - s * p.cps;
+  ShiftStream t = shift_stream<V>(p, s);
+  for (; c < c_end; ++c) {
+    const int64_t j = k * kPer + lane;
+    const uint64_t c_lo = t.b_lo + (uint64_t)j;
+    const uint64_t c_hi = t.b_hi + ((c_lo < t.b_lo) ? 1u : 0u);
     const uint4 b = philox4x32_10(ctr_from(c_lo, c_hi), p.rk);
-    const uint32_t n0 = __shfl_down_sync(0xFFFFFFFFu, b.x, 1);
-    const uint32_t n1 = __shfl_down_sync(0xFFFFFFFFu, b.y, 1);
-    const uint32_t n2 = __shfl_down_sync(0xFFFFFFFFu, b.z, 1);
-    uint4 w = b;
-    if (ph == 1) {
-      w = make_uint4(b.y, b.z, b.w, n0);
-    } else if (ph == 2) {
-      w = make_uint4(b.z, b.w, n0, n1);
-    } else if (ph == 3) {
-      w = make_uint4(b.w, n0, n1, n2);
-    }
-    const uint4 v = block_outputs<V>(w, p.t);
-    uint4 o = v;
+    uint4 o = block_outputs<V>(shift_words(b, t.ph), p.t);
     if constexpr (I::epu == 2) {
-      const uint32_t m0 = __shfl_down_sync(0xFFFFFFFFu, v.x, 1);
-      const uint32_t m1 = __shfl_down_sync(0xFFFFFFFFu, v.y, 1);
-      if (split) o = I::es == 4 ? make_uint4(v.y, v.z, v.w, m0) : make_uint4(v.z, v.w, m0, m1);
+      const uint4 sg = split_group<V>(o);  // shuffles: every lane takes part
+      if (t.split) o = sg;
     }
-    if (lane < kMultiShiftPer && j < groups) {
-      const int64_t e0 = j * kEpg - (int64_t)head;
+    if (k * kPer >= t.jf && k * kPer + kPer <= t.jl) {  // whole groups (uniform)
+      if (lane < kPer) t.gbase[j] = o;
+    } else if (lane < kPer && j < t.groups) {
+      const int64_t e0 = j * kEpg - t.head;
       if (e0 >= 0 && e0 + kEpg <= p.n) {
-        gbase[j] = o;
+        t.gbase[j] = o;
       } else {
-        store_partial<V>(sbase, e0, p.n, o);
+        store_partial<V>(t.sbase, e0, p.n, o);
       }
+    }
+    if (++k == p.cps) {
+      k = 0;
+      ++s;
+      if (c + 1 < c_end) t = shift_stream<V>(p, s);
     }
   }
 }
 
-// Resident CTAs per SM a launch may use: the occupancy, capped by the tuned
-// geometry when one is set.
-int ctas_cap(int occ, int32_t geom) { return geom > 0 && geom < occ ? (int)geom : occ; }
+// CTAs per SM a launch may use, from the tuned geometry: 1..16 a cap on the
+// resident CTAs; 17 and above (geom - 16) waves of resident CTAs, each CTA
+// taking that fraction of a resident CTA's share of the grid-stride loop, so
+// that the hardware refills an SM as its CTAs finish instead of the SM
+// emptying out as the faster warps of long-lived CTAs finish first (ncu: a
+// single persistent wave kept 33 of 48 possible warps active); 0, the
+// built-in choice, is 8 waves (within 1 % of the best wave count for every
+// fill at n = 10^9; one wave was up to 6 % slower).
+int ctas_cap(int occ, int32_t geom) {
+  if (geom == 0) return occ * 8;
+  if (geom > 16) return occ * (geom - 16);
+  return geom < occ ? (int)geom : occ;
+}
 
 template <typename K>
 int blocks_per_sm(K kernel) {
@@ -536,6 +585,8 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.n = r.n;
     p.head = head;
     p.groups = groups;
+    p.jf = head > 0 ? 1 : 0;
+    p.jl = ((head + r.n) % kEpg) != 0 ? groups - 1 : groups;
     p.rk = philox_round_keys(r.key[0], r.key[1]);
     if ((phase_w % (uint32_t)I::wpu) == 0) {
       launch_shift<V, false>(p, lo0, hi0, sms, geom, stream);

@@ -7,11 +7,12 @@
 // the geometry changes speed, never values.  The geometry of a fill is one
 // integer per (engine, kernel variant, size bucket), the bucket being the bit
 // length of n:
-//   Philox4x32-10: the cap on resident CTAs per SM of the grid (the kernels
-//     loop with a grid stride, so fewer CTAs give each thread more blocks);
+//   Philox4x32-10: the CTAs per SM of the grid, the kernels looping with a
+//     grid stride: 1..16 caps the resident CTAs (fewer CTAs give each thread
+//     more blocks), 17 and above launches (value - 16) waves of resident CTAs;
 //   MRG32k3a: the threads per SM of the chunk plan in units of 256 (the
 //     chunk length, hence the jump-ahead work per output, follows from it).
-// 0 keeps the launcher's built-in choice (Philox: every resident CTA;
+// 0 keeps the launcher's built-in choice (Philox: 8 waves of resident CTAs;
 // MRG32k3a: 2048 threads per SM).  The table starts from the file named by
 // the environment variable GRNG_TUNE_CACHE, if set, when it is first read;
 // grng_fill_autotune fills entries by timing, grng_tune_save / _load write and
@@ -147,10 +148,10 @@ grng_status grng_fill_autotune(int32_t engine_kind, const grng_distribution* dis
   grng_engine_t e = nullptr;
   st = grng_engine_create(&e, engine_kind, 0x5EEDu, 0);
   if (st != GRNG_OK) return st;
-  static const int32_t kPhilox[] = {0, 1, 2, 3, 4, 5, 6, 8};
+  static const int32_t kPhilox[] = {0, 1, 2, 4, 17, 18, 20, 32, 48, 64};
   static const int32_t kMrg[] = {0, 1, 2, 4, 6, 12, 16};
   const int32_t* cand = engine_kind == GRNG_PHILOX4X32X10 ? kPhilox : kMrg;
-  const int ncand = engine_kind == GRNG_PHILOX4X32X10 ? 8 : 7;
+  const int ncand = engine_kind == GRNG_PHILOX4X32X10 ? 10 : 7;
   std::call_once(g_env_once, load_env);
   std::atomic<int32_t>& slot = g_geom[engine_kind][v][bucket_of(n)];
   const int32_t before = slot.load(std::memory_order_relaxed);

@@ -367,7 +367,7 @@ def test_every_fill_geometry_gives_the_same_outputs(g, engine_kind):
     """Every launch geometry the fill autotuner tries gives the same words, bit
     for bit (outputs depend on the word index only); after tuning, fills
     still equal the oracle."""
-    cands = [0, 1, 2, 3, 4, 5, 6, 8] if engine_kind == 0 else [0, 1, 2, 4, 6, 12, 16]
+    cands = [0, 1, 2, 4, 17, 18, 20, 32, 48, 64] if engine_kind == 0 else [0, 1, 2, 4, 6, 12, 16]
     g.tune_reset()
     try:
         for var in [VARIANTS[0], VARIANTS[4], VARIANTS[7], VARIANTS[10], VARIANTS[12]]:
@@ -394,3 +394,28 @@ def test_every_fill_geometry_gives_the_same_outputs(g, engine_kind):
             assert_parity(kind, dtype, got.view(np.uint32) if dtype == 0 else got, ref, var[0])
     finally:
         g.tune_reset()
+
+
+@pytest.mark.parametrize("engine_kind,stride", [(1, (1 << 76) + 1), (0, (1 << 40) + 3)])
+@pytest.mark.parametrize("var", [VARIANTS[7], VARIANTS[9], VARIANTS[0], VARIANTS[4]],
+                         ids=["gauss_f32", "logn_f64", "bits", "u01_f64"])
+def test_odd_length_substreams_at_every_phase(g, engine_kind, stride, var):
+    """64 substreams of an odd length from a misaligned base, at a word stride
+    that is not a multiple of 4: every stream starts at its own 16-byte phase
+    and word phase (and, for the Box-Muller fills, every other stream splits a
+    pair), over many chunks per stream; streams compared in full with the
+    oracle."""
+    _, kind, dtype, p0, p1 = var
+    S, n = 64, 100_003
+    buf = torch.full((S * n + 2,), 0, dtype=_torch_dtype(dtype), device="cuda")
+    out = buf[1:1 + S * n]
+    e = g.Engine(engine_kind, 77, 9)
+    g.generate_substreams(g.Distribution(kind, dtype, p0, p1), e, out, n, S, stride)
+    torch.cuda.synchronize()
+    host = out.cpu().numpy()
+    assert e.offset == 9
+    for s in list(range(0, S, 9)) + [S - 1]:
+        ref = oracle.generate(engine_kind, 77, 9 + s * stride, kind, dtype, p0, p1, n)
+        got = host[s * n:(s + 1) * n]
+        assert_parity(kind, dtype, got.view(np.uint32) if dtype == 0 else got, ref,
+                      f"{var[0]} stream {s}")
