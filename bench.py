@@ -326,12 +326,31 @@ def run_config1(grng, torch, dev, stream, reps=50):
             grng.generate(d, e, out, stream=stream)
             host.append(time.perf_counter() - t0)
         torch.cuda.synchronize()
+        # ten launches captured in a CUDA graph: the kernel's own time at this
+        # size, without the host's per-call work between launches
+        g10 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g10, stream=stream):
+            for _ in range(10):
+                grng.generate(d, e, out, stream=stream)
+        g10.replay()
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        for a, b in gev:
+            a.record(stream)
+            g10.replay()
+            b.record(stream)
+        torch.cuda.synchronize()
+        del g10
+    ms_graph = statistics.median(a.elapsed_time(b) for a, b in gev) / 10
     ms = statistics.median(a.elapsed_time(b) for a, b in ev)
     return {"workload": "Philox4x32-10 seed 0x12345678 offset 0: 2^20 FP32 uniforms [0,1)",
             "device_us": round(ms * 1e3, 2), "gsamples_s": round(n / ms / 1e6, 2),
             "write_gbs": round(4 * n / ms / 1e6, 1),
             "host_call_us": round(statistics.median(host) * 1e6, 2), "reps": reps,
-            "note": "4 MB: launch and ramp-up bound, far below the HBM roofline"}
+            "graph_device_us_per_launch": round(ms_graph * 1e3, 2),
+            "graph_gsamples_s": round(n / ms_graph / 1e6, 2),
+            "note": "4 MB: launch and ramp-up bound, far below the HBM roofline; device_us "
+                    "includes the gap while the host issues the call, graph_* do not"}
 
 
 def run_config3(grng, torch, dev, stream, hbm_peak, reps=3):
