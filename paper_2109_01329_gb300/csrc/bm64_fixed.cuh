@@ -127,6 +127,22 @@ GRNG_BM_HD void mul64x32(uint64_t a, uint32_t c, uint64_t& hi, uint32_t& lo32) {
   lo32 = (uint32_t)l;
 }
 
+// Round-to-nearest conversions between uint32 and float.
+GRNG_BM_HD float u32_to_f32(uint32_t x) {
+#if defined(__CUDA_ARCH__)
+  return __uint2float_rn(x);
+#else
+  return (float)x;
+#endif
+}
+GRNG_BM_HD uint32_t f32_to_u32_rn(float x) {
+#if defined(__CUDA_ARCH__)
+  return __float2uint_rn(x);
+#else
+  return (uint32_t)std::nearbyint(x);
+#endif
+}
+
 GRNG_BM_HD float bits_f32(uint32_t b) {
   float f;
   std::memcpy(&f, &b, 4);
@@ -252,12 +268,16 @@ GRNG_BM_HD void neg_log(uint64_t m1, uint64_t& lm, int& le) {
   const uint32_t q = mulh(r32, r32);
   const uint32_t t = mulh(q, r32);
   const uint32_t u = mulh(q, q);
-  const uint32_t v = mulh(u, r32);
-  const uint32_t w = mulh(u, q);
   const uint64_t T3 = mulw(t, 0xAAAAAAABu) >> 28;              // t 2^5 / 3
-  const uint32_t T456 = (u >> 6) +                              // u / 2^6
-                        (mulh(v, 0x33333333u) >> 13) +          // v / (5 2^13)
-                        (mulh(w, 0x2AAAAAABu) >> 22);           // w / (6 2^22)
+  // r^5/5 + r^6/6 are below 2^17 units of 2^-64, so FP32 is exact enough
+  // (error below 2^-6 units) and keeps them off the integer multiplier, the
+  // busiest pipe: with x = r 2^9 < 1, 2^64 (r^5/5 + r^6/6) = x^5 (2^19/5 +
+  // x 2^10/6)
+  const float x = u32_to_f32(r32) * 0x1p-32f;
+  const float x2 = x * x;
+  const float x5 = x2 * x2 * x;
+  const uint32_t T456 = (u >> 6) +                              // u / 2^6 = r^4/4 2^64
+                        f32_to_u32_rn(x5 * fma32(x, 170.66667f, 104857.6f));
   const uint64_t S = R + (sqr_hi(R) >> 1) + T3 + T456;
   // -ln(1 - delta) 2^64 = ln c_i 2^64 + S < ln 2 2^64 + 2^55; with e >= 1
   // the sum e ln 2 + ... is kept in units of 2^-58 (below 37 2^58 < 2^64)
@@ -325,9 +345,11 @@ GRNG_BM_HD void sincos_turns(uint64_t x2, uint64_t& c_abs, bool& c_neg, uint64_t
   const uint64_t P2 = sqr_hi(P);                    // phi^2 2^64 < 2^43.4
   const uint32_t a = (uint32_t)(P2 >> 12);          // phi^2 2^52
   const uint32_t b = (uint32_t)(P >> 22);           // phi 2^42
-  // phi^4/24 2^64 = (a^2 2^-32) / 6144 and phi^3/6 2^64 = (a b 2^-32) 2/3;
-  // both need under 28 significant bits (phi^5/120 2^64 < 41 is dropped)
-  const uint32_t Q4 = mulh(mulh(a, a), 699051u);
+  // phi^3/6 2^64 = (a b 2^-32) 2/3 needs under 28 significant bits (phi^5/120
+  // 2^64 < 41 is dropped)
+  // phi^4/24 2^64 = a^2 2^-40 / 24, below 2^18: in FP32 (error below 2^-6)
+  const float af = u32_to_f32(a);
+  const uint32_t Q4 = f32_to_u32_rn(af * af * 0x1.5555555555556p-45f);
   const uint32_t Q3 = mulh(mulh(a, b), 2863311531u);
   const uint64_t eps = (P2 >> 1) - Q4;              // (1 - cos phi) 2^64
   const uint64_t sphi = P - Q3;                     // sin phi 2^64, >= eps
