@@ -202,10 +202,10 @@ def oracle_rate(seconds_per_case: float, cores: int, n_cap: int):
 # implemented: Philox4x32-10 is 20 products per 4-word block; an MRG32k3a word
 # is 7 (per component two multiplier products, then the folds of 2^32 = c
 # mod m: one 32-bit product for m1, one wide and one 32-bit product for m2);
-# the fixed-point FP64 Box-Muller pair is 36 products (log: 8, square root:
+# the fixed-point FP64 Box-Muller pair is 35 products (log: 7, square root:
 # 6, sine and cosine: 16, the two final products: 6) on top of the products
 # of its 4 words.
-BM64_PRODUCTS_PER_PAIR = 36
+BM64_PRODUCTS_PER_PAIR = 35
 
 # DRAM bytes (read + write) per launch at n = 10^9 from ncu captures of the
 # current kernels: one launch of 2.68e8 samples scaled by 1e9 / 2.68e8;

@@ -262,22 +262,20 @@ GRNG_BM_HD void neg_log(uint64_t m1, uint64_t& lm, int& le) {
   mul64x32(M, C, mc_hi, mc_lo);
   const uint64_t R = 0ull - ((mc_hi << 8) | (uint64_t)(mc_lo >> 24));  // < 2^55
   // -ln(1 - r) 2^64 = R + R^2/2 + T3 + T4 + T5 + T6 (r^7/7 < 2^-65.8).
-  // With r32 = r 2^41 the higher powers come from 32-bit high products:
-  // q = r^2 2^50, t = r^3 2^59, u = r^4 2^68, v = r^5 2^77, w = r^6 2^86.
+  // With r32 = r 2^41, r^3 comes from 32-bit high products: q = r^2 2^50,
+  // t = r^3 2^59.
   const uint32_t r32 = (uint32_t)(R >> 23);
   const uint32_t q = mulh(r32, r32);
   const uint32_t t = mulh(q, r32);
-  const uint32_t u = mulh(q, q);
   const uint64_t T3 = mulw(t, 0xAAAAAAABu) >> 28;              // t 2^5 / 3
-  // r^5/5 + r^6/6 are below 2^17 units of 2^-64, so FP32 is exact enough
-  // (error below 2^-6 units) and keeps them off the integer multiplier, the
-  // busiest pipe: with x = r 2^9 < 1, 2^64 (r^5/5 + r^6/6) = x^5 (2^19/5 +
-  // x 2^10/6)
+  // r^4/4 + r^5/5 + r^6/6 stay below 2^26 units of 2^-64, so FP32 is exact
+  // enough (error about 4 units) and keeps them off the integer multiplier,
+  // the busiest pipe: with x = r 2^9 < 1, 2^64 (r^4/4 + r^5/5 + r^6/6) =
+  // x^4 (2^26 + x (2^19/5 + x 2^10/6))
   const float x = u32_to_f32(r32) * 0x1p-32f;
   const float x2 = x * x;
-  const float x5 = x2 * x2 * x;
-  const uint32_t T456 = (u >> 6) +                              // u / 2^6 = r^4/4 2^64
-                        f32_to_u32_rn(x5 * fma32(x, 170.66667f, 104857.6f));
+  const uint32_t T456 =
+      f32_to_u32_rn(x2 * x2 * fma32(x, fma32(x, 170.66667f, 104857.6f), 67108864.0f));
   const uint64_t S = R + (sqr_hi(R) >> 1) + T3 + T456;
   // -ln(1 - delta) 2^64 = ln c_i 2^64 + S < ln 2 2^64 + 2^55; with e >= 1
   // the sum e ln 2 + ... is kept in units of 2^-58 (below 37 2^58 < 2^64)
