@@ -259,3 +259,28 @@ def test_tune_table_save_load_reset(g, tmp_path):
     with pytest.raises(g.GrngError):
         g.fill_geometry(2, d32, 100, 1)
     g.tune_reset()
+
+
+def test_tune_cache_from_the_environment(g, tmp_path):
+    """A cache file named by GRNG_TUNE_CACHE is read when the table is first
+    used (in a fresh process); a missing file is no error."""
+    import subprocess
+    import sys
+
+    path = tmp_path / "cache.txt"
+    d = g.Distribution.uniform(0.0, 1.0, g.F32)
+    g.tune_reset()
+    g.fill_geometry(1, d, 5000, 6)
+    g.tune_save(str(path))
+    g.tune_reset()
+    code = ("import paper_2109_01329_gb300 as g; "
+            "d = g.Distribution.uniform(0.0, 1.0, g.F32); "
+            "print(g.fill_geometry(1, d, 5000), g.fill_geometry(0, d, 5000))")
+    env = dict(os.environ, GRNG_TUNE_CACHE=str(path))
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=120, check=True).stdout.split()
+    assert out == ["6", "0"]
+    env["GRNG_TUNE_CACHE"] = str(tmp_path / "missing.txt")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=120, check=True).stdout.split()
+    assert out == ["0", "0"]
