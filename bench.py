@@ -328,10 +328,14 @@ def run_config1(grng, torch, dev, stream, reps=50):
         torch.cuda.synchronize()
         # ten launches captured in a CUDA graph: the kernel's own time at this
         # size, without the host's per-call work between launches
+        # (captured on a stream of its own: capture needs a non-default stream)
         g10 = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g10, stream=stream):
+        cap = torch.cuda.Stream(device=dev)
+        cap.wait_stream(stream)
+        with torch.cuda.graph(g10, stream=cap):
             for _ in range(10):
-                grng.generate(d, e, out, stream=stream)
+                grng.generate(d, e, out, stream=cap)
+        stream.wait_stream(cap)
         g10.replay()
         gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(reps)]
@@ -429,6 +433,21 @@ def run_offset_paths(grng, torch, dev, n, buf, stream, reps=3):
         res[f"{en}/substreams_gaussian_f32"] = {k: round(v, 4) for k, v in times.items()}
         res[f"{en}/substreams_gaussian_f32"]["ratio"] = round(
             times["odd_len_odd_stride"] / times["aligned"], 3)
+    # one stream at word offsets 1, 2, 3 (the groups straddle counter blocks or
+    # MRG32k3a units), a fresh engine per call
+    for ek, en in ENGINES:
+        for name, kind, dtype, p0, p1 in (("bits", 0, 0, 0.0, 0.0), ("uniform_f32", 1, 1, 0.0, 1.0)):
+            out = buf[: n * 4].view(torch.int32 if dtype == 0 else torch.float32)
+            d = grng.Distribution(kind, dtype, p0, p1)
+            times = {}
+            for off in (0, 1, 2, 3):
+                times[f"word_offset_{off}"] = _event_ms(
+                    torch, stream, lambda: grng.generate(d, grng.Engine(ek, W.SWEEP_SEED, off),
+                                                         out, stream=stream), reps)
+            key = f"{en}/{name}_word_offsets"
+            res[key] = {k: round(v, 4) for k, v in times.items()}
+            res[key]["worst_ratio"] = round(
+                max(times[f"word_offset_{o}"] for o in (1, 2, 3)) / times["word_offset_0"], 3)
     # the batched table, outputs at element offset 0 and 1
     table = W.batched_requests(4096)
     tdt = {0: torch.int32, 1: torch.float32, 2: torch.float64}

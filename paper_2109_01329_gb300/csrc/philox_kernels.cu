@@ -182,8 +182,26 @@ __host__ __device__ constexpr int shift_per_warp() {
   return kSplit ? 30 : 31;
 }
 
-// The 4 words of a group whose first word is at phase ph of block b (this
-// lane's), the rest from the next lane's block.
+// The 4 words of a group whose first word is at phase kPh (1..3) of block b
+// (this lane's), the rest from the next lane's block; kPh a constant, so only
+// the kPh words needed cross lanes.
+template <int kPh>
+__device__ __forceinline__ uint4 shift_words_c(uint4 b) {
+  const uint32_t n0 = __shfl_down_sync(0xFFFFFFFFu, b.x, 1);
+  if constexpr (kPh == 1) {
+    return make_uint4(b.y, b.z, b.w, n0);
+  } else {
+    const uint32_t n1 = __shfl_down_sync(0xFFFFFFFFu, b.y, 1);
+    if constexpr (kPh == 2) {
+      return make_uint4(b.z, b.w, n0, n1);
+    } else {
+      const uint32_t n2 = __shfl_down_sync(0xFFFFFFFFu, b.z, 1);
+      return make_uint4(b.w, n0, n1, n2);
+    }
+  }
+}
+
+// The same with the phase ph known only at run time (warp-uniform).
 __device__ __forceinline__ uint4 shift_words(uint4 b, uint32_t ph) {
   const uint32_t n0 = __shfl_down_sync(0xFFFFFFFFu, b.x, 1);
   const uint32_t n1 = __shfl_down_sync(0xFFFFFFFFu, b.y, 1);
@@ -203,7 +221,8 @@ __device__ __forceinline__ uint4 split_group(uint4 v) {
   return VInfo<V>::es == 4 ? make_uint4(v.y, v.z, v.w, m0) : make_uint4(v.z, v.w, m0, m1);
 }
 
-template <int V, int U, bool kHiUniform, bool kSplit>
+// kPh: the word phase as a constant (1..3), or -1 to read it from p.ph.
+template <int V, int U, bool kHiUniform, bool kSplit, int kPh>
 __device__ __forceinline__ void philox_shift_body(const ShiftParams& p) {
   using I = VInfo<V>;
   constexpr int kEpg = 16 / I::es;
@@ -231,7 +250,12 @@ __device__ __forceinline__ void philox_shift_body(const ShiftParams& p) {
     const bool interior = c * kPer >= p.jf && (c + (U - 1) * TW) * kPer + kPer <= p.jl;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const uint4 w = (!kSplit || p.ph != 0) ? shift_words(b[u], p.ph) : b[u];
+      uint4 w;
+      if constexpr (kPh < 0) {
+        w = shift_words(b[u], p.ph);
+      } else {
+        w = shift_words_c<kPh>(b[u]);
+      }
       // every lane transforms its (virtual) group; in split mode lane l + 1's
       // first element is needed by lane l
       uint4 o = block_outputs<V>(w, p.t);
@@ -253,14 +277,34 @@ __device__ __forceinline__ void philox_shift_body(const ShiftParams& p) {
   }
 }
 
+// The phase is the same for the whole grid.  Raw bits take one loop per
+// phase, each with the phase a constant (n = 10^9 at phases 1, 2, 3: 0.764,
+// 0.771, 0.796 ms against 0.852, 0.851, 0.915 with the phase a variable).  The
+// transformed variants keep the variable phase: with a constant phase 1 the
+// FP32 uniform ran 10 % slower (ncu: 207 against 186 million instructions,
+// the words moved into place one by one where the variable form selects each
+// into place), while phases 2 and 3 gained 4-8 %.
+template <int V, int U, bool kHiUniform, bool kSplit>
+__device__ __forceinline__ void philox_shift_phases(const ShiftParams& p) {
+  if constexpr (V == V_BITS && !kSplit) {
+    switch (p.ph) {
+      case 1: philox_shift_body<V, U, kHiUniform, kSplit, 1>(p); break;
+      case 2: philox_shift_body<V, U, kHiUniform, kSplit, 2>(p); break;
+      default: philox_shift_body<V, U, kHiUniform, kSplit, 3>(p); break;
+    }
+  } else {
+    philox_shift_body<V, U, kHiUniform, kSplit, -1>(p);
+  }
+}
+
 template <int V, int U, bool kHiUniform, bool kSplit>
 __global__ void __launch_bounds__(kThreads) philox_shift_kernel(const __grid_constant__ ShiftParams p) {
-  philox_shift_body<V, U, kHiUniform, kSplit>(p);
+  philox_shift_phases<V, U, kHiUniform, kSplit>(p);
 }
 
 template <int V, int U, bool kHiUniform, bool kSplit>
 __global__ void __launch_bounds__(kThreads, 5) philox_shift_kernel_5(const __grid_constant__ ShiftParams p) {
-  philox_shift_body<V, U, kHiUniform, kSplit>(p);
+  philox_shift_phases<V, U, kHiUniform, kSplit>(p);
 }
 
 // ------------------------------------------------------------ substreams

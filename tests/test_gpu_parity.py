@@ -122,6 +122,25 @@ def test_small_cases_all_variants(g, engine_kind, var):
         assert_parity(var[1], var[2], got, ref, f"{var[0]} n={n} off={off} ptr+{pofs}")
 
 
+@pytest.mark.parametrize("ph", [1, 2, 3])
+def test_philox_bits_at_each_word_phase(g, ph):
+    """Philox bits whose groups start at word phase 1, 2 or 3 of a counter
+    block (a loop of its own per phase): a long fill, at an aligned and a
+    misaligned pointer, equals the aligned fill's words moved by the offset,
+    and a fill across the 2^64 carry of the block counter equals the oracle."""
+    var = VARIANTS[0]
+    n = (1 << 22) + 3
+    ref = _gpu_fill(g, 0, 2021, 0, var, n + 8)
+    for pofs in (0, 1, 3):
+        off = (ph + pofs) % 4 + 4  # the groups' word phase is off - pofs mod 4
+        got = _gpu_fill(g, 0, 2021, off, var, n, ptr_off=pofs)
+        bad = np.nonzero(got != ref[off:off + n])[0]
+        assert bad.size == 0, f"phase {ph} ptr+{pofs}: {bad.size} differ, first at {bad[:5]}"
+    off = (1 << 66) - 4 * 1000 + ph
+    got = _gpu_fill(g, 0, 7, off, var, 100003)
+    assert_parity(0, 0, got, _ref(0, 7, off, var, 100003), f"2^64 block carry, phase {ph}")
+
+
 def test_philox_uniform_2pow20_bit_exact(g):
     c = W.PHILOX_UNIFORM_2POW20
     var = c["dist"]
