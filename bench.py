@@ -212,8 +212,10 @@ BM64_PRODUCTS_PER_PAIR = 35
 # a kernel whose code changed after its capture is left out (no number
 # rather than a stale one).
 NCU_TRAFFIC_PER_1E9 = {
-    "mrg32k3a/gaussian_f64": (2.082773e9 + 0.145e6) / 0.268,
-    "philox4x32_10/gaussian_f64": (2.083048e9 + 0.280e6) / 0.268,
+    "mrg32k3a/gaussian_f64": (2.083401e9 + 0.486e6) / 0.268,
+    "philox4x32_10/gaussian_f64": (2.082358e9 + 0.304e6) / 0.268,
+    "philox4x32_10/uniform_f32": (1.010112e9 + 0.043e6) / 0.268,
+    "philox4x32_10/uniform_f64": (2.082500e9 + 0.099e6) / 0.268,
 }
 
 # The method's own 32x32 -> 64-bit products per sample, independent of how
@@ -954,7 +956,10 @@ def run_ours(args):
         "write_gbs": target["write_gbs"], "frac": target["frac_roofline"],
         "frac_hbm_copy_peak": target["frac_hbm"],
         "frac_write_only_probe": target["frac_write_probe"],
-        "write_only_probe_gbs": round(write_gbs, 1), "meets_0_80": target["frac_roofline"] >= 0.80}
+        "write_only_probe_gbs": round(write_gbs, 1), "meets_0_80": target["frac_roofline"] >= 0.80,
+        "bytes_per_launch": n * 4,
+        "traffic": (round(NCU_TRAFFIC_PER_1E9["philox4x32_10/uniform_f32"] * n / 1e9)
+                    if "philox4x32_10/uniform_f32" in per_kernel else None)}
 
     # cuRAND on the same fills (generate calls only; generator created outside)
     curand = None
