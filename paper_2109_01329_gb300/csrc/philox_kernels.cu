@@ -280,10 +280,11 @@ __device__ __forceinline__ void philox_shift_body(const ShiftParams& p) {
 // The phase is the same for the whole grid.  Raw bits take one loop per
 // phase, each with the phase a constant (n = 10^9 at phases 1, 2, 3: 0.764,
 // 0.771, 0.796 ms against 0.852, 0.851, 0.915 with the phase a variable).  The
-// transformed variants keep the variable phase: with a constant phase 1 the
-// FP32 uniform ran 10 % slower (ncu: 207 against 186 million instructions,
-// the words moved into place one by one where the variable form selects each
-// into place), while phases 2 and 3 gained 4-8 %.
+// FP32 uniforms take the constant form for phases 2 and 3 only: with a
+// constant phase 1 they ran 10 % slower (ncu: 207 against 186 million
+// instructions, the words moved into place one by one where the variable form
+// selects each into place), while phases 2 and 3 gained 4-8 %.  The other
+// variants keep the variable phase.
 template <int V, int U, bool kHiUniform, bool kSplit>
 __device__ __forceinline__ void philox_shift_phases(const ShiftParams& p) {
   if constexpr (V == V_BITS && !kSplit) {
@@ -291,6 +292,12 @@ __device__ __forceinline__ void philox_shift_phases(const ShiftParams& p) {
       case 1: philox_shift_body<V, U, kHiUniform, kSplit, 1>(p); break;
       case 2: philox_shift_body<V, U, kHiUniform, kSplit, 2>(p); break;
       default: philox_shift_body<V, U, kHiUniform, kSplit, 3>(p); break;
+    }
+  } else if constexpr ((V == V_U01_F32 || V == V_UNI_F32) && !kSplit) {
+    switch (p.ph) {
+      case 2: philox_shift_body<V, U, kHiUniform, kSplit, 2>(p); break;
+      case 3: philox_shift_body<V, U, kHiUniform, kSplit, 3>(p); break;
+      default: philox_shift_body<V, U, kHiUniform, kSplit, -1>(p); break;
     }
   } else {
     philox_shift_body<V, U, kHiUniform, kSplit, -1>(p);

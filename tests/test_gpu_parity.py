@@ -123,22 +123,24 @@ def test_small_cases_all_variants(g, engine_kind, var):
 
 
 @pytest.mark.parametrize("ph", [1, 2, 3])
-def test_philox_bits_at_each_word_phase(g, ph):
-    """Philox bits whose groups start at word phase 1, 2 or 3 of a counter
-    block (a loop of its own per phase): a long fill, at an aligned and a
-    misaligned pointer, equals the aligned fill's words moved by the offset,
-    and a fill across the 2^64 carry of the block counter equals the oracle."""
-    var = VARIANTS[0]
+@pytest.mark.parametrize("var", VARIANTS[:3], ids=[v[0] for v in VARIANTS[:3]])
+def test_philox_one_word_fills_at_each_word_phase(g, ph, var):
+    """Philox fills of one word per output (bits, FP32 uniforms) whose groups
+    start at word phase 1, 2 or 3 of a counter block (loops of their own per
+    phase): a long fill, at an aligned and a misaligned pointer, equals the
+    aligned fill moved by the offset, and a fill across the 2^64 carry of the
+    block counter equals the oracle."""
     n = (1 << 22) + 3
     ref = _gpu_fill(g, 0, 2021, 0, var, n + 8)
     for pofs in (0, 1, 3):
         off = (ph + pofs) % 4 + 4  # the groups' word phase is off - pofs mod 4
         got = _gpu_fill(g, 0, 2021, off, var, n, ptr_off=pofs)
-        bad = np.nonzero(got != ref[off:off + n])[0]
+        bad = np.nonzero(_as_uint_view(got) != _as_uint_view(ref[off:off + n]))[0]
         assert bad.size == 0, f"phase {ph} ptr+{pofs}: {bad.size} differ, first at {bad[:5]}"
     off = (1 << 66) - 4 * 1000 + ph
     got = _gpu_fill(g, 0, 7, off, var, 100003)
-    assert_parity(0, 0, got, _ref(0, 7, off, var, 100003), f"2^64 block carry, phase {ph}")
+    assert_parity(var[1], var[2], got, _ref(0, 7, off, var, 100003),
+                  f"2^64 block carry, phase {ph}")
 
 
 def test_philox_uniform_2pow20_bit_exact(g):
