@@ -314,6 +314,160 @@ __global__ void __launch_bounds__(kThreads, 5) philox_shift_kernel_5(const __gri
   philox_shift_phases<V, U, kHiUniform, kSplit>(p);
 }
 
+// ------------------------------------------------------ single stream, rotated
+// One stream whose units lie inside counter blocks (the word offset a multiple
+// of the words per unit) while its output start is not at the blocks' 16-byte
+// phase.  Block j's four output words are then output words 4 j - r .. 4 j -
+// r + 3 (r = word offset mod 4): the last kS = (h - r) mod 4 of them open the
+// next 16-byte group (h: output words of out's group before out).  Each lane
+// transforms its own block once and completes its group from the last kS
+// output words of lane - 1 by shuffle; lane 0 writes only its own part of its
+// group and lane 31 the opening words of the next group, with 4- or 8-byte
+// stores at constant offsets from the group's address, so a warp writes 32
+// groups per 32 blocks and no unit is transformed twice (the shift kernel's
+// split form transforms 2 virtual groups in 32 twice).
+struct RotateParams {
+  TransformParams t;
+  uint4* gbase;       // out's 16-byte group
+  char* out;          // element 0
+  int64_t nw;         // output words: n es / 4
+  int64_t h;          // output words of out's group before out
+  int64_t r;          // word offset mod 4
+  int64_t gofs;       // the group lane l completes is out's group + j + gofs (0 or -1)
+  int64_t chunks;     // ceil(blocks / 32)
+  uint64_t base_lo;   // block holding the stream's first word
+  uint64_t base_hi;
+  uint32_t s;         // the rotation kS, 1..3
+  PhiloxRoundKeys rk;
+};
+
+// (lane - 1's last kS output words, this lane's first 4 - kS)
+template <int kS>
+__device__ __forceinline__ uint4 rotate_up(uint4 o) {
+  const uint32_t n3 = __shfl_up_sync(0xFFFFFFFFu, o.w, 1);
+  if constexpr (kS == 1) {
+    return make_uint4(n3, o.x, o.y, o.z);
+  } else {
+    const uint32_t n2 = __shfl_up_sync(0xFFFFFFFFu, o.z, 1);
+    if constexpr (kS == 2) {
+      return make_uint4(n2, n3, o.x, o.y);
+    } else {
+      const uint32_t n1 = __shfl_up_sync(0xFFFFFFFFu, o.y, 1);
+      return make_uint4(n1, n2, n3, o.x);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t word_of(uint4 v, int q) {
+  return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+}
+
+// Positions [q0, q1) of the 16-byte group at g, position q taking word
+// q + kFrom of v; 8-byte elements go out whole (q0 and q1 even for them).
+template <int V, int q0, int q1, int kFrom>
+__device__ __forceinline__ void store_positions(uint4* g, uint4 v) {
+  if constexpr (VInfo<V>::es == 4) {
+#pragma unroll
+    for (int q = q0; q < q1; ++q) reinterpret_cast<uint32_t*>(g)[q] = word_of(v, q + kFrom);
+  } else {
+#pragma unroll
+    for (int q = q0; q < q1; q += 2)
+      reinterpret_cast<uint2*>(g)[q >> 1] = make_uint2(word_of(v, q + kFrom), word_of(v, q + kFrom + 1));
+  }
+}
+
+// The same with each output word checked against [0, nw) (edge chunks).
+template <int V, int q0, int q1, int kFrom>
+__device__ __forceinline__ void store_positions_checked(const RotateParams& p, int64_t G, uint4 v) {
+  constexpr int kStep = VInfo<V>::es / 4;
+#pragma unroll
+  for (int q = q0; q < q1; q += kStep) {
+    const int64_t i = 4 * G + q - p.h;
+    if (i >= 0 && i < p.nw) {
+      if constexpr (kStep == 1) {
+        reinterpret_cast<uint32_t*>(p.out)[i] = word_of(v, q + kFrom);
+      } else {
+        reinterpret_cast<uint2*>(p.out)[i >> 1] =
+            make_uint2(word_of(v, q + kFrom), word_of(v, q + kFrom + 1));
+      }
+    }
+  }
+}
+
+template <int V, int U, bool kHiUniform, int kS>
+__device__ __forceinline__ void philox_rotate_body(const RotateParams& p) {
+  const int lane = threadIdx.x & 31;
+  const int64_t TW = (int64_t)gridDim.x * (kThreads / 32);
+  const int64_t c0 = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  // lane l of chunk c holds block j = 32 c + l; j, the counter and the group
+  // address advance by increments (dj from chunk c to c + TW)
+  const int64_t dj = TW * 32;
+  int64_t j = c0 * 32 + lane;
+  uint64_t lo = p.base_lo + (uint64_t)j;
+  uint4* dst = p.gbase + (j + p.gofs);
+  // the loop bound depends only on the warp: every shuffle has all 32 lanes
+  for (int64_t c = c0; c < p.chunks;
+       c += U * TW, j += U * dj, lo += (uint64_t)(U * dj), dst += U * dj) {
+    uint4 b[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t l = lo + (uint64_t)(u * dj);
+      const uint64_t hh = kHiUniform ? p.base_hi : p.base_hi + ((l < p.base_lo) ? 1u : 0u);
+      b[u] = philox4x32_10(ctr_from(l, hh), p.rk);
+    }
+    // every output word of this iteration's chunks lies inside the output
+    // (uniform): words 128 c - r .. 128 c' + 127 - r, c' the last chunk
+    const bool interior = c * 128 - p.r >= 0 && (c + (U - 1) * TW) * 128 + 127 - p.r < p.nw;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint4 o = block_outputs<V>(b[u], p.t);
+      const uint4 g = rotate_up<kS>(o);
+      if (interior) {
+        uint4* gp = dst + u * dj;
+        if (lane > 0) {
+          *gp = g;
+        } else {
+          store_positions<V, kS, 4, 0>(gp, g);
+        }
+        if (lane == 31) store_positions<V, 0, kS, 4 - kS>(gp + 1, o);
+      } else {
+        const int64_t G = j + u * dj + p.gofs;
+        if (lane > 0) {
+          store_positions_checked<V, 0, 4, 0>(p, G, g);
+        } else {
+          store_positions_checked<V, kS, 4, 0>(p, G, g);
+        }
+        if (lane == 31) store_positions_checked<V, 0, kS, 4 - kS>(p, G + 1, o);
+      }
+    }
+  }
+}
+
+// The rotation is the same for the whole grid: one loop per rotation, each
+// with it a constant (8-byte elements rotate by one element only).
+template <int V, int U, bool kHiUniform>
+__device__ __forceinline__ void philox_rotate_phases(const RotateParams& p) {
+  if constexpr (VInfo<V>::es == 8) {
+    philox_rotate_body<V, U, kHiUniform, 2>(p);
+  } else {
+    switch (p.s) {
+      case 1: philox_rotate_body<V, U, kHiUniform, 1>(p); break;
+      case 2: philox_rotate_body<V, U, kHiUniform, 2>(p); break;
+      default: philox_rotate_body<V, U, kHiUniform, 3>(p); break;
+    }
+  }
+}
+
+template <int V, int U, bool kHiUniform>
+__global__ void __launch_bounds__(kThreads) philox_rotate_kernel(const __grid_constant__ RotateParams p) {
+  philox_rotate_phases<V, U, kHiUniform>(p);
+}
+
+template <int V, int U, bool kHiUniform>
+__global__ void __launch_bounds__(kThreads, 5) philox_rotate_kernel_5(const __grid_constant__ RotateParams p) {
+  philox_rotate_phases<V, U, kHiUniform>(p);
+}
+
 // ------------------------------------------------------------ substreams
 // num_streams streams whose every group is full (16-byte aligned streams of
 // whole groups); stream s, group j is block base + s * sb + j.
@@ -528,6 +682,53 @@ void launch_shift(ShiftParams& p, uint64_t a_lo, uint64_t a_hi, int sms, int32_t
   (hi_uniform ? k_uni : k_carry)<<<(unsigned)grid, kThreads, 0, stream>>>(p);
 }
 
+// Launches the rotate kernel (units inside blocks, output start at another
+// phase); p.t, p.out, p.gbase, p.nw, p.h, p.rk are set by the caller.
+template <int V>
+void launch_rotate(RotateParams& p, uint64_t off_lo, uint64_t off_hi, int sms, int32_t geom,
+                   cudaStream_t stream) {
+  constexpr int kU = blocks_per_thread<V>();
+  p.r = (int64_t)(off_lo & 3u);
+  const int64_t d = p.h - p.r;
+  p.s = (uint32_t)((d + 4) & 3);
+  p.gofs = d < 0 ? -1 : 0;
+  p.base_lo = (off_lo >> 2) | (off_hi << 62);
+  p.base_hi = off_hi >> 2;
+  const int64_t blocks = (p.nw - 1 + p.r) / 4 + 1;
+  p.chunks = (blocks + 31) / 32;
+  void (*k_uni)(const RotateParams);
+  void (*k_carry)(const RotateParams);
+  // the FP64 Box-Muller variants gain from a fifth CTA as in the stream
+  // kernel; the FP32 ones would spill under its register cap here
+  if constexpr (stream_wants_5_ctas<V>() && VInfo<V>::es == 8) {
+    k_uni = philox_rotate_kernel_5<V, kU, true>;
+    k_carry = philox_rotate_kernel_5<V, kU, false>;
+  } else {
+    k_uni = philox_rotate_kernel<V, kU, true>;
+    k_carry = philox_rotate_kernel<V, kU, false>;
+  }
+  static std::atomic<int> occ[2] = {{0}, {0}};
+  int o = occ[0].load(std::memory_order_relaxed);
+  if (o == 0) {
+    o = blocks_per_sm(k_uni);
+    occ[0].store(o, std::memory_order_relaxed);
+    occ[1].store(blocks_per_sm(k_carry), std::memory_order_relaxed);
+  }
+  const int64_t warps = (p.chunks + kU - 1) / kU;
+  int64_t grid = (warps + (kThreads / 32) - 1) / (kThreads / 32);
+  if (grid < 1) grid = 1;
+  const int64_t cap = (int64_t)sms * ctas_cap(o, geom);
+  if (grid > cap) grid = cap;
+  // blocks touched: below (chunks + kU * warps in flight) * 32 past base
+  const uint64_t reach = (uint64_t)(p.chunks + (int64_t)kU * grid * (kThreads / 32) + 1) * 32u;
+  const bool hi_uniform = p.base_lo + reach >= p.base_lo;
+  if (!hi_uniform) {
+    const int64_t cap2 = (int64_t)sms * ctas_cap(occ[1].load(std::memory_order_relaxed), geom);
+    if (grid > cap2) grid = cap2;
+  }
+  (hi_uniform ? k_uni : k_carry)<<<(unsigned)grid, kThreads, 0, stream>>>(p);
+}
+
 template <int V>
 grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
   using I = VInfo<V>;
@@ -626,6 +827,19 @@ grng_status launch_variant(const FillRequest& r, cudaStream_t stream) {
     p.tqsb_lo = (uint64_t)tqsb;
     p.tqsb_hi = (uint64_t)(tqsb >> 64);
     philox_multi_kernel<V><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+  } else if (I::wpu >= 2 && r.num_streams == 1 && (r.off_lo % (uint64_t)I::wpu) == 0) {
+    // one stream whose units lie inside counter blocks, the output start at
+    // another phase (e.g. a Box-Muller pair split by the pointer)
+    if constexpr (I::wpu >= 2) {
+      RotateParams p;
+      p.t = r.t;
+      p.out = reinterpret_cast<char*>(r.out);
+      p.gbase = reinterpret_cast<uint4*>(addr - phase_w * 4u);
+      p.nw = r.n * (I::es / 4);
+      p.h = (int64_t)phase_w;
+      p.rk = philox_round_keys(r.key[0], r.key[1]);
+      launch_rotate<V>(p, r.off_lo, r.off_hi, sms, geom, stream);
+    }
   } else if (r.num_streams == 1 &&
              ((phase_w % (uint32_t)I::wpu) == 0 || (I::epu == 2 && (head & 1) != 0))) {
     // one stream at another word phase, or a pair split by the output's start

@@ -110,6 +110,7 @@ SMALL_CASES = [
     (1, 0, 0), (2, 0, 1), (3, 1, 0), (5, 2, 3), (7, 3, 2), (64, 0, 0), (1000, 5, 1),
     (4099, 0, 0), (4099, 2, 2), (70001, 3, 1), (262147, 0, 0), (33, (1 << 34) - 7, 0),
     (101, (1 << 64) - 9, 3), (97, (1 << 76) * 3 + 1, 1), (50, (1 << 128) - 30, 0),
+    (1001, 2, 1), (65537, 4, 3), (4133, (1 << 66) - 4 * 517 + 2, 1),
 ]
 
 
@@ -141,6 +142,39 @@ def test_philox_one_word_fills_at_each_word_phase(g, ph, var):
     got = _gpu_fill(g, 0, 7, off, var, 100003)
     assert_parity(var[1], var[2], got, _ref(0, 7, off, var, 100003),
                   f"2^64 block carry, phase {ph}")
+
+
+# variants of two or four words per unit: with the word offset a multiple of
+# that, the units lie inside counter blocks and a misaligned output start only
+# rotates each block's outputs across two 16-byte groups
+MULTIWORD_VARIANTS = [v for v in VARIANTS
+                      if v[1] in (2, 3) or (v[2] == 2 and v[1] in (1, 4, 5))]
+
+
+@pytest.mark.parametrize("engine_kind", ENGINES)
+@pytest.mark.parametrize("var", MULTIWORD_VARIANTS, ids=[v[0] for v in MULTIWORD_VARIANTS])
+def test_misaligned_output_equals_aligned_output(g, engine_kind, var):
+    """A fill written at every element offset into a 16-byte group, from word
+    offsets that keep the units inside counter blocks (Philox: the rotate
+    kernel, lane 0 and lane 31 writing the groups shared by two warps), equals
+    the same fill written at an aligned address bit for bit; near the 2^64
+    carry of the block counter it equals the oracle."""
+    _, kind, dtype, p0, p1 = var
+    wpu = 4 if (kind in (2, 3) and dtype == 2) else 2
+    es = 8 if dtype == 2 else 4
+    n = (1 << 21) + 7
+    for off in (0, wpu, 6 * wpu):
+        ref = _gpu_fill(g, engine_kind, 2021, off, var, n)
+        for pofs in range(1, 16 // es):
+            got = _gpu_fill(g, engine_kind, 2021, off, var, n, ptr_off=pofs)
+            bad = np.nonzero(_as_uint_view(got) != _as_uint_view(ref))[0]
+            assert bad.size == 0, f"{var[0]} off={off} ptr+{pofs}: {bad.size} differ, " \
+                                  f"first at {bad[:5]}"
+    off = (1 << 66) - 4 * 3000
+    for pofs in range(1, 16 // es):
+        got = _gpu_fill(g, engine_kind, 11, off, var, 20001, ptr_off=pofs)
+        assert_parity(kind, dtype, got, _ref(engine_kind, 11, off, var, 20001),
+                      f"{var[0]} 2^64 block carry ptr+{pofs}")
 
 
 def test_philox_uniform_2pow20_bit_exact(g):
