@@ -18,6 +18,12 @@
 //     neighbouring lanes by shuffle.  When the output's start splits a
 //     Box-Muller pair, lanes transform pair-aligned groups one element
 //     earlier and exchange the straddling element too (30 groups per warp).
+//   * rotate kernel (one stream of 2- or 4-word units at a word offset
+//     that keeps them inside blocks, the output start at another 16-byte
+//     phase): each lane transforms its own block and rotates its outputs
+//     into the group that lane - 1's block opens, by shuffle; lane 0 and
+//     lane 31 write the groups shared with the neighbouring warps' chunks
+//     with narrower stores, so no unit is transformed twice.
 //   * multi-shift kernel: substreams at another phase or alignment, the
 //     shift kernel's exchange applied per stream (a warp works on 30 groups
 //     of one stream).
