@@ -36,7 +36,10 @@ def nvcc() -> str:
 
 
 def _flags(ptxas_verbose: bool) -> list[str]:
-    f = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+    # host code keeps every multiply and add rounded on its own (no fused
+    # forms), as the device code's explicit round-to-nearest intrinsics do
+    f = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "-I", INCLUDE, "-I", CSRC,
          "-Xcompiler", "-fvisibility=hidden"] + ARCH
     if ptxas_verbose:
         f += ["-Xptxas", "-v"]

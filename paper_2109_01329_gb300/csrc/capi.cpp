@@ -193,6 +193,49 @@ bool exact_affine_f64(double a, double b, int64_t* A, int32_t* e) {
   return true;
 }
 
+// The integer form of the F64 uniform's product d u (u = x 2^-53): d's
+// 53-bit significand and exponent, when every nonzero product is a normal
+// double; and the clamp as a threshold on x.  a + d u with its two roundings
+// is non-decreasing in x, so r >= b holds exactly from the smallest such x on;
+// the host evaluates the same two roundings (volatile: never fused).
+void uniform_f64_consts(double a, double b, TransformParams* t) {
+  const double d = t->dd;
+  int k = 0;
+  const double f = std::frexp(d, &k);  // d = f 2^k, f in [0.5, 1)
+  if (std::isfinite(d) && d > 0.0 && k >= -960) {
+    const uint64_t D = (uint64_t)std::ldexp(f, 53);  // [2^52, 2^53)
+    t->rd_hi = (uint32_t)(D >> 32);
+    t->rd_lo = (uint32_t)D;
+    t->rd_exp = k - 53;
+    t->r_int = 1;
+  }
+  auto reaches = [&](uint64_t x) {
+    volatile double u = std::ldexp((double)x, -53);
+    volatile double prod = d * u;
+    volatile double r = a + prod;
+    return r >= b;
+  };
+  const uint64_t top = (uint64_t(1) << 53) - 1;
+  if (!reaches(top)) {
+    t->r_xthr = uint64_t(1) << 53;
+    return;
+  }
+  uint64_t lo = 0, hi = top;  // reaches(hi); the threshold is in (lo, hi] unless reaches(0)
+  if (reaches(0)) {
+    t->r_xthr = 0;
+    return;
+  }
+  while (hi - lo > 1) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    if (reaches(mid)) {
+      hi = mid;
+    } else {
+      lo = mid;
+    }
+  }
+  t->r_xthr = hi;
+}
+
 int choose_variant(const grng_distribution* d, TransformParams* t) {
   std::memset(t, 0, sizeof(*t));
   switch (d->kind) {
@@ -219,6 +262,7 @@ int choose_variant(const grng_distribution* d, TransformParams* t) {
           t->aff_exp = e;
           return V_AFF_F64;
         }
+        uniform_f64_consts(a, b, t);
         return V_UNI_F64;
       }
     case GRNG_GAUSSIAN:

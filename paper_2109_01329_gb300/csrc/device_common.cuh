@@ -132,6 +132,37 @@ __device__ __forceinline__ double u01_f64(uint32_t wa, uint32_t wb) {
   return __hiloint2double((int)(mh + (1032u << 20) - (c << 20)), (int)ml);
 }
 
+// d u rounded to nearest (even), u = x 2^-53, x = (xh 2^32 + xl) with
+// xh != 0, for d = D 2^e (D = rd_hi 2^32 + rd_lo in [2^52, 2^53)), whose
+// nonzero products are normal doubles (checked on the host): the same value
+// as the FP64 multiply, from four 32 x 32 products.  With X = x << s in
+// [2^52, 2^53), P = D X lies in [2^104, 2^106); its top 53 bits, rounded on
+// the next bit and the OR of all lower ones (ties to even), are the
+// significand m, and the bit pattern is m + (E - 1) 2^52 (the leading one of
+// m completes the biased exponent E; a carry out of rounding moves into the
+// exponent by itself).
+__device__ __forceinline__ double mul_rn_u53(uint32_t xh, uint32_t xl, const TransformParams& t) {
+  const uint32_t c = (uint32_t)__clz((int)xh);      // 11..31
+  const uint32_t s = c - 11u;
+  const uint32_t Xh = __funnelshift_l(xl, xh, s);   // [2^20, 2^21)
+  const uint32_t Xl = xl << s;
+  const uint64_t LL = (uint64_t)t.rd_lo * Xl;
+  const uint64_t M = (uint64_t)t.rd_lo * Xh + (uint64_t)t.rd_hi * Xl;  // < 2^54
+  const uint64_t mid = (LL >> 32) + (M & 0xFFFFFFFFull);                // < 2^33
+  const uint32_t w0 = (uint32_t)LL;
+  const uint32_t w1 = (uint32_t)mid;
+  const uint64_t U = (uint64_t)t.rd_hi * Xh + (M >> 32) + (mid >> 32);  // P >> 64
+  const bool top = (U >> 41) != 0;                                      // P >= 2^105
+  const uint32_t q = top ? 11u : 12u;
+  const uint64_t m0 = (U << q) | (uint64_t)(w1 >> (32u - q));           // P >> (64 - q)
+  const uint32_t rb = (w1 >> (31u - q)) & 1u;
+  const uint32_t sticky = (w1 & ((1u << (31u - q)) - 1u)) | w0;
+  const uint64_t m = m0 + (uint64_t)(rb & ((sticky != 0u) | (uint32_t)(m0 & 1u)));
+  // t = m 2^(e - s) (top) or m 2^(e - s - 1): E = that exponent + 1075
+  const int64_t E = (int64_t)t.rd_exp - (int64_t)s - (top ? 0 : 1) + 1075;
+  return __longlong_as_double((long long)(m + ((uint64_t)(E - 1) << 52)));
+}
+
 // ---------------------------------------------------------- range transform
 // Sec. 4.3, Listing 2 computes acc * (b - a) + a in a second kernel; here it
 // is fused, with explicit round-to-nearest multiply and add (never
@@ -140,9 +171,24 @@ __device__ __forceinline__ float range_f32(float u, const TransformParams& t) {
   const float r = __fadd_rn(t.fa, __fmul_rn(t.fd, u));
   return r >= t.fb ? t.fbprev : r;
 }
-__device__ __forceinline__ double range_f64(double u, const TransformParams& t) {
-  const double r = __dadd_rn(t.da, __dmul_rn(t.dd, u));
-  return r >= t.db ? t.dbprev : r;
+// The FP64 form for the words (w_a, w_b) of x: the product in integers (one
+// FP64 operation, the add, remains; a product, add and compare on this
+// part's narrow FP64 pipe took 3.4x the [0, 1) fill's time), the clamp as
+// the host's threshold on x.  x < 2^32 (probability 2^-21) and ranges whose
+// products can leave the normal doubles take the FP64 product.
+__device__ __forceinline__ double uniform_ab_f64(uint32_t wa, uint32_t wb,
+                                                 const TransformParams& t) {
+  const uint32_t xh = wa >> 11;
+  const uint32_t xl = __funnelshift_r(wb, wa, 11);
+  double prod;
+  if (t.r_int != 0 && xh != 0) {
+    prod = mul_rn_u53(xh, xl, t);
+  } else {
+    prod = __dmul_rn(t.dd, u01_f64(wa, wb));
+  }
+  const double r = __dadd_rn(t.da, prod);
+  const uint64_t x = ((uint64_t)xh << 32) | xl;
+  return x >= t.r_xthr ? t.dbprev : r;
 }
 
 // -------------------------------------------------------------- Box-Muller
@@ -293,7 +339,7 @@ __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
     } else if constexpr (V == V_AFF_F64) {
       r = scaled_i54_to_f64(t.aff_a + (int64_t)u53(w[0], w[1]), t.aff_exp);
     } else {
-      r = range_f64(u01_f64(w[0], w[1]), t);
+      r = uniform_ab_f64(w[0], w[1], t);
     }
     const uint64_t b = (uint64_t)__double_as_longlong(r);
     o[0] = (uint32_t)b;

@@ -55,6 +55,13 @@ struct TransformParams {
   float fa, fd, fb, fbprev;   // F32 uniform: a, b - a, b, largest float below b
   float fmean, fsd;           // F32 gaussian (mean, sd) / lognormal (m, s)
   double da, dd, db, dbprev;  // F64 uniform
+  // F64 uniform on [a, b) with the product d u in integers: d = (rd_hi 2^32 +
+  // rd_lo) 2^rd_exp, its 53-bit significand; r_int = 0 keeps the FP64
+  // product; r_xthr = the smallest 53-bit x whose a + d x 2^-53 (two
+  // roundings) reaches b, 2^53 if none
+  uint32_t rd_hi, rd_lo;
+  int32_t rd_exp, r_int;
+  uint64_t r_xthr;
   double dmean, dsd;          // F64 gaussian / lognormal
   int64_t aff_a;              // F64 exact affine: r = (aff_a + x) 2^aff_exp, x = 53-bit word
   int32_t aff_exp;

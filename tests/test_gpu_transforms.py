@@ -137,8 +137,12 @@ def test_fp64_lognormal_ranges(g, m, s):
 def test_fp64_uniform_edges(g):
     w = _fp64_edge_pairs(seed=2, n_random=50000)
     n = w.size // 2
+    # the product d u in integers (ordinary ranges) and on the FP64 pipe (ranges
+    # whose products can be subnormal), the clamp as a threshold on the words
     for a, b in [(0.0, 1.0), (-1.0, 1.0), (-0.5, 0.5), (2.0, 5.0), (-1e300, 1e300),
-                 (0.25, 0.5), (-4.0, 0.0)]:
+                 (0.25, 0.5), (-4.0, 0.0), (-3.0, 7.5), (0.1, 0.7), (1e15, 1e15 + 3.0),
+                 (1.0, 1.0 + 2.0**-40), (3.0, 3.0000000000000004), (-7.25, -7.0),
+                 (-1e-300, 1e-300), (0.0, 2.0**-1000), (-2.0**-1060, 2.0**-1060)]:
         got = _gpu(g, 1, 2, a, b, w, n)
         ref = oracle.transform_words(1, 2, a, b, n, w)
         _check(1, 2, got, ref, f"FP64 uniform [{a}, {b})")
