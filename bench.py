@@ -301,6 +301,7 @@ EXTRA_DISTS = [
     ("icdf_gaussian_f32", 4, 1, 0.0, 1.0), ("icdf_lognormal_f32", 5, 1, 0.0, 1.0),
     ("icdf_gaussian_f64", 4, 2, 0.0, 1.0), ("lognormal_f64", 3, 2, 0.0, 1.0),
     ("gaussian_f64_m3_s0.25", 2, 2, -3.0, 0.25), ("uniform_f32_2_5", 1, 1, 2.0, 5.0),
+    ("uniform_f64_2_5", 1, 2, 2.0, 5.0),
 ]
 
 

@@ -176,12 +176,16 @@ __device__ __forceinline__ float range_f32(float u, const TransformParams& t) {
 // part's narrow FP64 pipe took 3.4x the [0, 1) fill's time), the clamp as
 // the host's threshold on x.  x < 2^32 (probability 2^-21) and ranges whose
 // products can leave the normal doubles take the FP64 product.
+// kInt = false takes the FP64 product for every x: the fill kernels pass it
+// for every second unit, so the integer pipes and the FP64 pipe share the
+// products (a constant after unrolling; both forms give the same bits).
+template <bool kInt>
 __device__ __forceinline__ double uniform_ab_f64(uint32_t wa, uint32_t wb,
                                                  const TransformParams& t) {
   const uint32_t xh = wa >> 11;
   const uint32_t xl = __funnelshift_r(wb, wa, 11);
   double prod;
-  if (t.r_int != 0 && xh != 0) {
+  if (kInt && t.r_int != 0 && xh != 0) {
     prod = mul_rn_u53(xh, xl, t);
   } else {
     prod = __dmul_rn(t.dd, u01_f64(wa, wb));
@@ -323,9 +327,11 @@ __device__ __forceinline__ uint32_t icdf_out_f32(float z, const TransformParams&
 
 // ------------------------------------------------- one unit -> its outputs
 // Writes the output words (4 bytes each) of one unit from its words.
+// odd: the unit's index in its block or chunk is odd (only the F64 uniform on
+// [a, b) looks at it, to alternate where its product is computed)
 template <int V>
 __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
-                                             const TransformParams& t) {
+                                             const TransformParams& t, bool odd = false) {
   if constexpr (V == V_BITS) {
     o[0] = w[0];
   } else if constexpr (V == V_U01_F32) {
@@ -339,7 +345,7 @@ __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
     } else if constexpr (V == V_AFF_F64) {
       r = scaled_i54_to_f64(t.aff_a + (int64_t)u53(w[0], w[1]), t.aff_exp);
     } else {
-      r = uniform_ab_f64(w[0], w[1], t);
+      r = odd ? uniform_ab_f64<false>(w[0], w[1], t) : uniform_ab_f64<true>(w[0], w[1], t);
     }
     const uint64_t b = (uint64_t)__double_as_longlong(r);
     o[0] = (uint32_t)b;
@@ -439,7 +445,7 @@ __device__ __forceinline__ uint4 block_outputs(uint4 b, const TransformParams& t
     for (int u = 0; u < 4; ++u) o[u] = icdf_out_f32<V>(icdf_f32_finish(c[u]), t);
   } else {
 #pragma unroll
-    for (int u = 0; u < 4 / kWpu; ++u) unit_outputs<V>(w + u * kWpu, o + u * kWpu, t);
+    for (int u = 0; u < 4 / kWpu; ++u) unit_outputs<V>(w + u * kWpu, o + u * kWpu, t, (u & 1) != 0);
   }
   return make_uint4(o[0], o[1], o[2], o[3]);
 }

@@ -164,12 +164,13 @@ __device__ __forceinline__ void jump(MrgRegs& s, uint64_t e_lo, uint64_t e_hi) {
 
 // Generates one unit's words and writes its kWpu output words to o.
 template <int V>
-__device__ __forceinline__ void gen_unit(MrgRegs& st, uint32_t* o, const TransformParams& t) {
+__device__ __forceinline__ void gen_unit(MrgRegs& st, uint32_t* o, const TransformParams& t,
+                                         bool odd = false) {
   constexpr int kWpu = VInfo<V>::wpu;
   uint32_t w[kWpu];
 #pragma unroll
   for (int i = 0; i < kWpu; ++i) w[i] = mrg_next(st);
-  unit_outputs<V>(w, o, t);
+  unit_outputs<V>(w, o, t, odd);
 }
 
 // The 16-byte stage chunk from 4 new output words: as they are, or (carry
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(kThreads) mrg_fill_kernel(const MrgParams p) {
         for (int ch = 0; ch < 8; ++ch) {
           uint32_t o4[4];
 #pragma unroll
-          for (int u = 0; u < kUpc; ++u) gen_unit<V>(st, o4 + u * kWpu, p.t);
+          for (int u = 0; u < kUpc; ++u) gen_unit<V>(st, o4 + u * kWpu, p.t, (u & 1) != 0);
           stage[warp][lane][ch ^ (lane & 7)] = kCarry ? shift_in<true, kOwpe>(carry, o4)
                                                       : shift_in<false, kOwpe>(carry, o4);
         }
