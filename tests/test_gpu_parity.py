@@ -429,15 +429,20 @@ def test_every_fill_geometry_gives_the_same_outputs(g, engine_kind):
             _, kind, dtype, p0, p1 = var
             d = g.Distribution(kind, dtype, p0, p1)
             n = 1_000_003
-            outs = []
-            for geo in cands:
-                assert g.fill_geometry(engine_kind, d, n, geo) == geo
-                out = torch.empty(n, dtype=_torch_dtype(dtype), device="cuda")
-                g.generate(d, g.Engine(engine_kind, 2021, 5), out)
-                outs.append(out)
-            torch.cuda.synchronize()
-            for geo, o in zip(cands[1:], outs[1:]):
-                assert torch.equal(o.view(torch.uint8), outs[0].view(torch.uint8)), (var[0], geo)
+            # word offset 5 (the shift kernels), and word offset 4 written one
+            # element past a 16-byte boundary (Philox: the rotate kernel for
+            # the multi-word variants)
+            for off, pofs in ((5, 0), (4, 1)):
+                outs = []
+                for geo in cands:
+                    assert g.fill_geometry(engine_kind, d, n, geo) == geo
+                    out = torch.empty(n + pofs, dtype=_torch_dtype(dtype), device="cuda")[pofs:]
+                    g.generate(d, g.Engine(engine_kind, 2021, off), out)
+                    outs.append(out)
+                torch.cuda.synchronize()
+                for geo, o in zip(cands[1:], outs[1:]):
+                    assert torch.equal(o.view(torch.uint8), outs[0].view(torch.uint8)), \
+                        (var[0], off, geo)
             buf = torch.empty(n, dtype=_torch_dtype(dtype), device="cuda")
             geo, ms, ms0 = g.fill_autotune(engine_kind, d, buf)
             assert geo in cands and 0 < ms <= ms0 * 1.0001
