@@ -142,7 +142,9 @@ def test_fp64_uniform_edges(g):
     for a, b in [(0.0, 1.0), (-1.0, 1.0), (-0.5, 0.5), (2.0, 5.0), (-1e300, 1e300),
                  (0.25, 0.5), (-4.0, 0.0), (-3.0, 7.5), (0.1, 0.7), (1e15, 1e15 + 3.0),
                  (1.0, 1.0 + 2.0**-40), (3.0, 3.0000000000000004), (-7.25, -7.0),
-                 (-1e-300, 1e-300), (0.0, 2.0**-1000), (-2.0**-1060, 2.0**-1060)]:
+                 (-1e-300, 1e-300), (0.0, 2.0**-1000), (-2.0**-1060, 2.0**-1060),
+                 # b - a with a short significand: the product d u often ties
+                 (0.0, 3.0), (-1.0, 2.0), (0.5, 1.25), (1.0, 6.0), (-0.75, 0.625)]:
         got = _gpu(g, 1, 2, a, b, w, n)
         ref = oracle.transform_words(1, 2, a, b, n, w)
         _check(1, 2, got, ref, f"FP64 uniform [{a}, {b})")
