@@ -163,6 +163,18 @@ __device__ __forceinline__ double mul_rn_u53(uint32_t xh, uint32_t xl, const Tra
   return __longlong_as_double((long long)(m + ((uint64_t)(E - 1) << 52)));
 }
 
+// The same value with one FP64 add in place of the normalisation: with B the
+// double whose bits are 0x3FE 2^52 + (x mod 2^52), i.e. 1/2 + (x mod 2^52)
+// 2^-53, x 2^-53 is B when x >= 2^52 and B - 1/2 otherwise, both exact (no
+// rare path).  The fills use it for every second unit, so the otherwise idle
+// FP64 pipe takes half the conversions off the integer pipes.
+__device__ __forceinline__ double u01_f64_dadd(uint32_t wa, uint32_t wb) {
+  const uint32_t h = wa >> 11;                      // x >> 32: 21 bits
+  const uint32_t l = __funnelshift_r(wb, wa, 11);   // low 32 bits of x
+  const double B = __hiloint2double((int)((h & 0xFFFFFu) | 0x3FE00000u), (int)l);
+  return __dadd_rn(B, (h >> 20) != 0u ? 0.0 : -0.5);
+}
+
 // ---------------------------------------------------------- range transform
 // Sec. 4.3, Listing 2 computes acc * (b - a) + a in a second kernel; here it
 // is fused, with explicit round-to-nearest multiply and add (never
@@ -327,8 +339,8 @@ __device__ __forceinline__ uint32_t icdf_out_f32(float z, const TransformParams&
 
 // ------------------------------------------------- one unit -> its outputs
 // Writes the output words (4 bytes each) of one unit from its words.
-// odd: the unit's index in its block or chunk is odd (only the F64 uniform on
-// [a, b) looks at it, to alternate where its product is computed)
+// odd: the unit's index in its block or chunk is odd (only the F64 uniforms
+// look at it, to alternate the integer and the FP64 pipe)
 template <int V>
 __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
                                              const TransformParams& t, bool odd = false) {
@@ -341,7 +353,7 @@ __device__ __forceinline__ void unit_outputs(const uint32_t* w, uint32_t* o,
   } else if constexpr (V == V_U01_F64 || V == V_AFF_F64 || V == V_UNI_F64) {
     double r;
     if constexpr (V == V_U01_F64) {
-      r = u01_f64(w[0], w[1]);
+      r = odd ? u01_f64_dadd(w[0], w[1]) : u01_f64(w[0], w[1]);
     } else if constexpr (V == V_AFF_F64) {
       r = scaled_i54_to_f64(t.aff_a + (int64_t)u53(w[0], w[1]), t.aff_exp);
     } else {
