@@ -212,10 +212,10 @@ BM64_PRODUCTS_PER_PAIR = 35
 # a kernel whose code changed after its capture is left out (no number
 # rather than a stale one).
 NCU_TRAFFIC_PER_1E9 = {
-    "mrg32k3a/gaussian_f64": (2.083401e9 + 0.486e6) / 0.268,
-    "philox4x32_10/gaussian_f64": (2.082358e9 + 0.304e6) / 0.268,
-    "philox4x32_10/uniform_f32": (1.010112e9 + 0.043e6) / 0.268,
-    "philox4x32_10/uniform_f64": (2.082500e9 + 0.099e6) / 0.268,
+    "mrg32k3a/gaussian_f64": (2.083313e9 + 0.118e6) / 0.268,
+    "philox4x32_10/gaussian_f64": (2.082409e9 + 0.304e6) / 0.268,
+    "philox4x32_10/uniform_f32": (1.010023e9 + 0.042e6) / 0.268,
+    "philox4x32_10/uniform_f64": (2.081978e9 + 0.056e6) / 0.268,
 }
 
 # The method's own 32x32 -> 64-bit products per sample, independent of how
