@@ -25,7 +25,9 @@ __global__ void __launch_bounds__(256) transform_kernel(TransformParams t, const
 #pragma unroll
     for (int i = 0; i < I::wpu; ++i) w[i] = words[k * I::wpu + i];
     uint32_t o[I::wpu];
-    unit_outputs<V>(w, o, t);
+    // odd units take the other pipe's form as in the fill kernels (the same
+    // bits), so this kernel checks both forms
+    unit_outputs<V>(w, o, t, (k & 1) != 0);
 #pragma unroll
     for (int i = 0; i < I::wpu; ++i) {
       const int64_t ow = k * I::wpu + i;  // 4 output bytes per word

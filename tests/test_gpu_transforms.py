@@ -136,19 +136,24 @@ def test_fp64_lognormal_ranges(g, m, s):
 
 def test_fp64_uniform_edges(g):
     w = _fp64_edge_pairs(seed=2, n_random=50000)
-    n = w.size // 2
-    # the product d u in integers (ordinary ranges) and on the FP64 pipe (ranges
-    # whose products can be subnormal), the clamp as a threshold on the words
+    # the product d u in integers (ordinary ranges, even units) and on the FP64
+    # pipe (odd units, and ranges whose products can be subnormal), the clamp as
+    # a threshold on the words
     for a, b in [(0.0, 1.0), (-1.0, 1.0), (-0.5, 0.5), (2.0, 5.0), (-1e300, 1e300),
                  (0.25, 0.5), (-4.0, 0.0), (-3.0, 7.5), (0.1, 0.7), (1e15, 1e15 + 3.0),
                  (1.0, 1.0 + 2.0**-40), (3.0, 3.0000000000000004), (-7.25, -7.0),
                  (-1e-300, 1e-300), (0.0, 2.0**-1000), (-2.0**-1060, 2.0**-1060),
                  # b - a with a short significand: the product d u often ties
                  (0.0, 3.0), (-1.0, 2.0), (0.5, 1.25), (1.0, 6.0), (-0.75, 0.625)]:
-        got = _gpu(g, 1, 2, a, b, w, n)
-        ref = oracle.transform_words(1, 2, a, b, n, w)
-        _check(1, 2, got, ref, f"FP64 uniform [{a}, {b})")
-        assert np.all(got >= a) and np.all(got < b)
+        # every word pair at an even and at an odd unit index (the transform
+        # kernel, like the fills, alternates the integer and the FP64 forms)
+        for lead in (0, 1):
+            ww = np.concatenate([w[:2 * lead], w])
+            nn = ww.size // 2
+            got = _gpu(g, 1, 2, a, b, ww, nn)
+            ref = oracle.transform_words(1, 2, a, b, nn, ww)
+            _check(1, 2, got, ref, f"FP64 uniform [{a}, {b}) lead {lead}")
+            assert np.all(got >= a) and np.all(got < b)
 
 
 def test_fp32_uniform_all_2_24(g):
